@@ -1,0 +1,370 @@
+#!/usr/bin/env python3
+"""Throughput of the invertible 3D orientation-score transform on GB300.
+
+One step = forward transform U = W f plus exact inverse f_rec = W^-1 U of one
+synthetic 128^3 volume (12 spline tubes + noise) with N_o = 162 icosahedral
+orientations, L = 16 (complex64 scores, 2.72 GB, larger than L2).
+Metric: voxel-orientations per second = n^3 N_o / (t_fwd + t_inv).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Multi-GPU (torchrun, one rank per GPU): independent replicas, one volume per
+rank per step, no collective on the data path ("scaling": "weak").
+The reference arm (--impl reference) times the FP64 CPU oracle on a bounded
+sample of the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import csv
+import hashlib
+import io
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "splines128_no162"
+METRIC = "OS transform voxel·orientations/s (fwd+inv, FP32) at 128³×162; p50/p99 latency"
+UNIT = "voxel-orientations/s"
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--bf16", action="store_true", help="store U as bfloat16 pairs")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def _workload_setup():
+    from paper_1505_07690_gb300 import synth
+    w = synth.WORKLOADS[WORKLOAD]
+    return w, synth
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, pci_bus_id):
+        self.pci = pci_bus_id
+        self.proc = None
+        self.tmp = None
+
+    def start(self):
+        try:
+            self.tmp = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                   "-lms", "200"]
+            if self.pci:
+                cmd += ["-i", self.pci]
+            self.proc = subprocess.Popen(cmd, stdout=self.tmp, stderr=subprocess.DEVNULL)
+        except (OSError, ValueError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.tmp.flush()
+        self.tmp.seek(0)
+        rows = list(csv.reader(io.StringIO(self.tmp.read())))
+        self.tmp.close()
+        os.unlink(self.tmp.name)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# the oracle on a bounded sample (cpu_baseline and the reference arm)
+# ---------------------------------------------------------------------------
+def oracle_sample_rate(n_orient, repeats=1):
+    """Oracle forward + exact inverse of the workload volume with a subset of
+    ``n_orient`` of the 162 orientations (a bank of that subset); returns
+    (voxel-orientations/s, seconds, description)."""
+    import numpy as np
+    from oracle import os3d_oracle as O
+    w, synth = _workload_setup()
+    f = synth.workload_volume(WORKLOAD).astype(np.float64)
+    V = O.icosa_orientations(w["subdiv"])
+    half = len(V) // 2
+    idx = list(range(n_orient // 2)) + list(range(half, half + n_orient // 2))
+    bank = O.Bank(w["shape"], V[idx], O.Params(L=w["L"]))
+    bank.M()   # bank construction is outside the timed region, as on the GPU
+    t0 = time.perf_counter()
+    for _ in range(repeats):
+        U = O.forward(f, bank)
+        O.inverse(U, bank)
+    dt = time.perf_counter() - t0
+    nvox = int(np.prod(w["shape"]))
+    return nvox * len(idx) * repeats / dt, dt, f"{len(idx)} of 162 orientations at 128^3, fwd+inv"
+
+
+def run_reference(args):
+    world, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    per_step = 2
+    for _ in range(args.warmup):
+        oracle_sample_rate(per_step)
+    times = []
+    vals = []
+    for _ in range(args.steps):
+        v, dt, desc = oracle_sample_rate(per_step)
+        times.append(dt)
+        vals.append(v)
+    tot = sum(times)
+    import numpy as np
+    nvox = 128 ** 3
+    value = nvox * per_step * args.steps / tot
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "dims": [128, 128, 128], "n_o": 162, "L": 16,
+                   "step_sample": f"{per_step} of 162 orientations, fwd+inv"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": desc},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# roofline bookkeeping
+# ---------------------------------------------------------------------------
+def _source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1505_07690_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:12]
+
+
+def _ncu_traffic(kind):
+    """DRAM bytes per launch of ``kind`` from the committed ncu summary, if it
+    was taken on the current kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    src = _source_hash()
+    for line in open(path):
+        p = line.split()
+        if len(p) >= 4 and not line.startswith("#") and p[0] == kind and p[1] == WORKLOAD:
+            return float(p[3]) if p[2] == src else None
+    return None
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import numpy as np
+    import torch
+    world, rank, local = _dist()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    from paper_1505_07690_gb300 import build, os3d
+    if rank == 0 or not os.path.exists(os3d.LIB_PATH):
+        build.build()
+    if world > 1:
+        torch.distributed.barrier()
+
+    w, synth = _workload_setup()
+    dims = w["shape"]
+    f_np = synth.workload_volume(WORKLOAD, seed=0, batch_index=rank)
+    V = os3d.os3d_icosa_orientations(w["subdiv"])
+    n_o = len(V)
+    bank = os3d.os3d_make_wavelets(dims, V, os3d.os3d_default_params(L=w["L"]))
+    f = torch.from_numpy(f_np).cuda().unsqueeze(0)
+    U = os3d.new_score(bank, 1, bf16=args.bf16)
+    frec = torch.empty_like(f)
+    stream = torch.cuda.current_stream()
+    nvox = int(np.prod(dims))
+    esize = 4 if args.bf16 else 8
+
+    def step():
+        os3d.os3d_forward(bank, f, U)
+        os3d.os3d_inverse(bank, U, frec)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    # ---- timed region: K steps, device-side events, inputs resident in HBM
+    clocks = ClockSampler(torch.cuda.get_device_properties(local).pci_bus_id
+                          if hasattr(torch.cuda.get_device_properties(local), "pci_bus_id") else None)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    barrier()
+    clocks.start()
+    l0 = os3d.os3d_launch_count()
+    ev[0].record(stream)
+    for i in range(args.steps):
+        step()
+        ev[i + 1].record(stream)
+    torch.cuda.synchronize()
+    launches = os3d.os3d_launch_count() - l0
+    barrier()
+    clk = clocks.stop()
+    step_ms = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
+    total_ms = ev[0].elapsed_time(ev[-1])
+    t = torch.tensor([total_ms], device="cuda")
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    total_ms = float(t.item())
+    value = world * nvox * n_o * args.steps / (total_ms / 1e3)
+
+    # ---- end to end: host buffers through the public API, copies timed
+    f_host = torch.from_numpy(f_np).unsqueeze(0).pin_memory()
+    out_host = torch.empty_like(f_host).pin_memory()
+    f_dev = torch.empty_like(f)
+
+    def e2e_step():
+        f_dev.copy_(f_host, non_blocking=True)
+        os3d.os3d_forward(bank, f_dev, U)
+        os3d.os3d_inverse(bank, U, frec)
+        out_host.copy_(frec, non_blocking=True)
+
+    e2e_step()
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1)
+    t = torch.tensor([e2e_ms], device="cuda")
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    e2e_value = world * nvox * n_o * args.steps / (float(t.item()) / 1e3)
+
+    # ---- per-kernel durations (CUDA events around every launch, same stream)
+    os3d.os3d_profile_reset()
+    os3d.os3d_profile_enable(True)
+    for _ in range(args.steps):
+        step()
+    torch.cuda.synchronize()
+    os3d.os3d_profile_enable(False)
+    prof = os3d.os3d_profile_read()
+    algo = {  # algorithmic HBM bytes over K steps, per kernel kind
+        "xy_fwd_score": args.steps * n_o * nvox * esize,
+        "xy_inv_score": args.steps * n_o * nvox * esize,
+        "xy_fwd_real": args.steps * nvox * 4,
+        "xy_inv_real": args.steps * nvox * 4,
+    }
+    dom = max(prof.items(), key=lambda kv: kv[1][1])[0]
+    peaks, peak_kind = _peaks()
+    nl, ms = prof[dom]
+    if dom in algo and ms > 0:
+        achieved = algo[dom] / (ms / 1e3) / 1e9
+        roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peaks["hbm_gbs"],
+                "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
+                "traffic": _ncu_traffic(dom), "peak_source": peak_kind,
+                "bytes_per_launch": algo[dom] / max(nl, 1), "launch_ms": ms / max(nl, 1)}
+    else:
+        roof = {"bound": "alu", "kernel": dom, "achieved": None, "peak": None, "unit": "TFLOP/s",
+                "frac": None, "traffic": _ncu_traffic(dom), "launch_ms": ms / max(nl, 1)}
+    # whole-step HBM view: U written once and read once
+    step_bytes = 2 * n_o * nvox * esize + 4 * nvox * 4
+    kernels = {k: {"launches": v[0], "ms_per_step": v[1] / args.steps,
+                   "share": v[1] / max(sum(x[1] for x in prof.values()), 1e-9)}
+               for k, v in prof.items() if v[0]}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, dt, desc = oracle_sample_rate(8)
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{desc} ({dt:.1f} s, numpy FP64, single thread)"}
+
+    if rank == 0:
+        lat = sorted(step_ms)
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "dims": list(dims), "n_o": n_o, "L": w["L"],
+                       "batch_per_gpu": 1, "udtype": "bf16x2" if args.bf16 else "c64",
+                       "parallelism": f"replicas{world}",
+                       "l2": f"inputs larger than L2 (U = {n_o * nvox * esize / 1e9:.2f} GB)"},
+            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
+            "roofline": roof,
+            "step_hbm": {"bytes": step_bytes, "achieved_gbs": step_bytes / (total_ms / args.steps / 1e3) / 1e9},
+            "kernels": kernels,
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": nvox * 4,
+                    "d2h_bytes_per_step": nvox * 4},
+            "gpu_launches": launches,
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    args = _args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,180 @@
+/*
+ * os3d — invertible orientation scores of 3D images on one GB300 (sm_103a).
+ *
+ * C ABI of the transform of Janssen, Duits and Breeuwer, "Invertible
+ * Orientation Scores of 3D Images" (arXiv 1505.07690):
+ *   cake wavelets  psi_hat_i(w) = G(|w|) h(w_hat . n_i),  h = sum_l c_l P_l
+ *                  (Sec. 3.1 radial window and B-spline orientation
+ *                  distribution, Sec. 3.2 zonal SH fit, Funk transform,
+ *                  anti-symmetrisation and steering, Eq. Rotationh);
+ *   forward        U_i = IDFT[ f_hat conj(psi_hat_i) ]      (Eq. construction1Discrete);
+ *   exact inverse  f = Re IDFT[ max(M,eps)^-1 sum_i psi_hat_i DFT(U_i) ],
+ *                  M = sum_i |psi_hat_i|^2                   (Eq. Reconstruction1Discrete,
+ *                                                             clamp of Sec. 3.1);
+ *   adjoint        W^* G = Re IDFT[ sum_i psi_hat_i DFT(G_i) ] (Sec. 4.1, App. A).
+ *
+ * Discrete conventions: the DFT is unnormalised with kernel exp(-i w.x) (the
+ * paper's sign); w_j = 2 pi k_j / n_j on the signed DFT index, so the Nyquist
+ * frequency is rho_N = pi; psi_hat vanishes outside the ball |w| < pi (the
+ * ball-limited images of Sec. 2 with varrho = rho_N); at w = 0 the angular
+ * factor is the spherical mean c_0 of h. The continuous constants (2 pi)^(3/2)
+ * and d sigma = 4 pi / N_o cancel in the exact inverse and are absorbed into
+ * the normalisation kappa of c, chosen so that the spherical mean of
+ * sum_i h(w_hat . n_i)^2 is 1 (the paper's aim M ~ 1, Sec. 2).
+ *
+ * Layout: volumes are row-major (nz, ny, nx), x fastest. A score U holds
+ * batch x N_o volumes, index ((b * N_o + i) * nz + z) * ny * nx + y * nx + x,
+ * each element complex: OS3D_U_C64 = interleaved float (re, im) (8 bytes),
+ * OS3D_U_BF16X2 = interleaved bfloat16 (re, im), round to nearest even
+ * (4 bytes). Re U = line response, Im U = edge response (Sec. 3, requirement 6).
+ *
+ * Ownership: the caller owns every data buffer (device pointers). A bank owns
+ * its coefficients, M^-1 and one default workspace until os3d_destroy_bank.
+ * Ordering: every call that takes a stream only enqueues work on it and
+ * returns; none synchronises the device, except os3d_make_wavelets, which
+ * synchronises its own stream once (it copies the fitted coefficients back).
+ * Errors: every entry point returns an os3d_status; arguments are checked
+ * before any launch; nothing aborts or throws across the ABI.
+ * Devices: a bank belongs to the device that was current at its creation;
+ * calls on it must be made with that device current.
+ * Concurrency: calls that share a workspace (including the bank's default
+ * one, used when the workspace argument is NULL) must be ordered on one
+ * stream; give concurrent calls distinct workspaces of os3d_bank_info's
+ * workspace_bytes.
+ */
+#ifndef OS3D_H
+#define OS3D_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  OS3D_OK = 0,
+  OS3D_EINVAL = 1,       /* a NULL pointer, a size or a parameter out of range   */
+  OS3D_ENOMEM = 2,       /* device allocation failed                             */
+  OS3D_ECUDA = 3,        /* a CUDA call failed (launch or copy)                  */
+  OS3D_ETIMEOUT = 4,     /* reserved for bounded waits of the serving loop       */
+  OS3D_EUNSUPPORTED = 5  /* grid size without a compiled FFT plan                */
+} os3d_status;
+
+typedef enum { OS3D_U_C64 = 0, OS3D_U_BF16X2 = 1 } os3d_udtype;
+
+/* Wavelet parameters (Sec. 3.1 and 3.2; defaults from os3d_default_params). */
+typedef struct {
+  int k;            /* order of the B-spline orientation distribution A = B^k(theta/s_theta); 0..8 */
+  double s_theta;   /* angular width s_theta > 0                                     */
+  int L;            /* maximal Legendre / SH degree, 0..32                            */
+  int N;            /* order of the radial window g = M_N, 0..64                      */
+  double gamma;     /* inflection point of g at gamma * rho_N, 0 < gamma < 1          */
+  double eps;       /* clamp M -> max(M, eps) of the inverse, eps > 0                */
+  int fit_mode;     /* 1: least squares on the order-15 icosahedral tessellation
+                       (the paper's pseudo-inverse); 0: L2 projection (Gauss-Legendre) */
+  int block_slots;  /* orientation pairs per launch block, 0 = automatic, else 1..8  */
+} os3d_params;
+
+typedef struct os3d_bank os3d_bank; /* opaque, library-owned */
+
+/* Defaults: k = 2, s_theta = 0.7, L = 16, N = 8, gamma = 0.8, eps = 1e-4,
+ * fit_mode = 1, block_slots = 0. Host only. */
+os3d_status os3d_default_params(os3d_params* p);
+
+/* Orientation set of Sec. 2.1: an icosahedron (vertices: cyclic permutations
+ * of (0, +-1, +-phi), normalised) subdivided `subdiv` times by edge midpoints
+ * projected onto S^2: 12, 42, 162, 642 ... unit vectors; both members of every
+ * antipodal pair are kept. Order: the representatives (z > 0, or z = 0 and
+ * y > 0, or z = y = 0 and x > 0) by decreasing z, then increasing azimuth
+ * atan2(y, x) in (-pi, pi]; then their antipodes in the same order, so that
+ * n_{i + N_o/2} = -n_i. `out` (host) receives n_o x 3 doubles (x, y, z);
+ * `capacity` is its length in vectors. Host only; subdiv 0..4.
+ * Returns OS3D_EINVAL if subdiv is out of range or capacity is too small
+ * (then *n_o still receives the required count). */
+os3d_status os3d_icosa_orientations(int subdiv, double* out, int capacity, int* n_o);
+
+/* Builds the wavelet bank for a grid dims = {nz, ny, nx} and the orientation
+ * set `orient` (host, n_o x 3 doubles, unit vectors, x y z). Steps (all on
+ * the device current at the call, stream-ordered on `stream`):
+ *  (a1) zonal fit b_l of A (FP64 kernel), Funk transform c^e_l = 2 pi P_l(0) b_l,
+ *       anti-symmetrisation c^o_l = (1 - (-1)^l) b_l, c = kappa (c^e + c^o)
+ *       (Sec. 3.2);
+ *  (a3) M = G^2 sum_i h(w_hat . n_i)^2 in FP64 and the factors
+ *       G / n^3 and G / (n^3 max(M, eps)) stored as float (Sec. 2.1, 3.1).
+ * Antipodal pairs in `orient` are detected (|n_i + n_j| < 1e-9) and share
+ * one transform in the forward and inverse passes.
+ * Supported axis lengths: 16, 32, 48, 64, 96, 128, 160 (nz), with the
+ * (ny, nx) planes 16^2, 32^2, 48^2, 64^2, 96^2, 128^2 and 128 x 160.
+ * Errors: EINVAL (NULL, n_o < 1, a non-unit orientation, parameter out of
+ * range), EUNSUPPORTED (grid), ENOMEM, ECUDA. `stream` may be NULL (legacy
+ * default stream). */
+os3d_status os3d_make_wavelets(const int dims[3], const double* orient, int n_o,
+                               const os3d_params* p, void* stream, os3d_bank** out);
+
+/* Forward transform (a4, a5): U = W f for `batch` real volumes f (device,
+ * batch x nz x ny x nx float) into U (device, batch x N_o x nz x ny x nx,
+ * udtype). Valid for real f: an antipodal pair is written as U_b = conj(U_a).
+ * `workspace` (device, os3d_bank_info's workspace_bytes, 256-byte aligned)
+ * or NULL for the bank's own. Errors: EINVAL, ECUDA. */
+os3d_status os3d_forward(const os3d_bank* bank, const float* f, int batch, void* U,
+                         os3d_udtype udtype, void* workspace, void* stream);
+
+/* Exact inverse (a6): f_out = Re IDFT[ max(M,eps)^-1 sum_i psi_hat_i DFT(U_i) ]
+ * for `batch` scores U (device, layout as above) into f_out (device, float).
+ * Any U is accepted (not only ranges of W). Errors: EINVAL, ECUDA. */
+os3d_status os3d_inverse(const os3d_bank* bank, const void* U, os3d_udtype udtype, int batch,
+                         float* f_out, void* workspace, void* stream);
+
+/* Adjoint (a7): grad_f = Re IDFT[ sum_i psi_hat_i DFT(G_i) ] = Re W^* G for
+ * `batch` score-shaped G (device). For a real loss L(U) with G = dL/dconj(U)
+ * in PyTorch's convention this is dL/df. Errors: EINVAL, ECUDA. */
+os3d_status os3d_adjoint(const os3d_bank* bank, const void* G, os3d_udtype udtype, int batch,
+                         float* grad_f, void* workspace, void* stream);
+
+/* Sizes: workspace bytes one call needs, and device bytes of one volume's
+ * score (N_o x nz x ny x nx x 8). Host only. */
+os3d_status os3d_bank_info(const os3d_bank* bank, size_t* workspace_bytes,
+                           size_t* score_bytes_per_volume);
+
+/* Copies of bank data for inspection: the Legendre coefficients b (of A) and
+ * c (of h = h_Re + h_Im, normalised), L + 1 doubles each (host); and, on the
+ * device, M^-1 = 1/max(M, eps) inside the ball (0 outside) as nz*ny*nx
+ * floats, stream-ordered. Either output pointer may be NULL. */
+os3d_status os3d_bank_coefficients(const os3d_bank* bank, double* b, double* c);
+os3d_status os3d_bank_minv(const os3d_bank* bank, float* minv, void* stream);
+
+os3d_status os3d_destroy_bank(os3d_bank* bank);
+const char* os3d_status_string(os3d_status s);
+
+/* ---- diagnostics (no counterpart in the paper) ---------------------------
+ * Kernel kinds of the transform: the xy-passes (2D DFT of one z-plane with
+ * the score store or load fused) and the z-passes (DFT along z with the
+ * wavelet evaluation, the orientation sum or a per-voxel factor fused). */
+enum {
+  OS3D_KIND_XY_FWD_REAL = 0,   /* forward: DFT_xy of the real image            */
+  OS3D_KIND_XY_FWD_SCORE = 1,  /* forward: IDFT_xy and store of U_a, U_b       */
+  OS3D_KIND_XY_INV_SCORE = 2,  /* inverse: load of U_a, U_b and DFT_xy         */
+  OS3D_KIND_XY_INV_REAL = 3,   /* inverse: IDFT_xy and store of the real image */
+  OS3D_KIND_Z_FWD_PREP = 4,    /* forward: DFT_z and the factor G / n^3        */
+  OS3D_KIND_Z_FWD_SCORE = 5,   /* forward: wavelet evaluation and IDFT_z       */
+  OS3D_KIND_Z_INV_SCORE = 6,   /* inverse: DFT_z, wavelet and orientation sum  */
+  OS3D_KIND_Z_INV_FINAL = 7,   /* inverse: factor G / (n^3 max(M,eps)), IDFT_z */
+  OS3D_KIND_COUNT = 8
+};
+
+/* Number of kernels this library has launched in this process. Host only. */
+unsigned long long os3d_launch_count(void);
+
+/* While enabled (on != 0), each kernel launch is bracketed by two CUDA events
+ * recorded on its stream. os3d_profile_read synchronises on the recorded
+ * events and returns, for one kind, the launches and total milliseconds
+ * since the last os3d_profile_reset. */
+os3d_status os3d_profile_enable(int on);
+os3d_status os3d_profile_read(int kind, unsigned long long* launches, double* ms);
+os3d_status os3d_profile_reset(void);
+const char* os3d_kernel_kind_name(int kind);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* OS3D_H */

@@ -1,0 +1,760 @@
+// C-ABI of the orientation-score library: argument checks, host-side FP64
+// geometry (orientation sets, tessellation, quadrature, Chebyshev form of the
+// angular profile), bank construction and the launch sequence of the
+// forward, inverse and adjoint transforms.
+#include <algorithm>
+#include <atomic>
+#include <mutex>
+#include <array>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <new>
+#include <tuple>
+#include <vector>
+
+#include "../../include/os3d.h"
+#include "os3d_kernels.cuh"
+
+namespace os3d {
+// per-size launchers (os3d_sizes_*.cu)
+#define OS3D_DECL_Z(N) cudaError_t launch_z_##N(int, int, const ZArgs&, int, cudaStream_t);
+#define OS3D_DECL_XY(NY, NX) \
+  cudaError_t launch_xy_##NY##_##NX(int, int, const XYArgs&, int, int, cudaStream_t);
+OS3D_DECL_Z(16) OS3D_DECL_Z(32) OS3D_DECL_Z(48) OS3D_DECL_Z(64) OS3D_DECL_Z(96)
+OS3D_DECL_Z(128) OS3D_DECL_Z(160)
+OS3D_DECL_XY(16, 16) OS3D_DECL_XY(32, 32) OS3D_DECL_XY(48, 48) OS3D_DECL_XY(64, 64)
+OS3D_DECL_XY(96, 96) OS3D_DECL_XY(128, 128) OS3D_DECL_XY(128, 160)
+
+bool z_supported(int nz) {
+  return nz == 16 || nz == 32 || nz == 48 || nz == 64 || nz == 96 || nz == 128 || nz == 160;
+}
+bool xy_supported(int ny, int nx) {
+  return (ny == nx && (nx == 16 || nx == 32 || nx == 48 || nx == 64 || nx == 96 || nx == 128)) ||
+         (ny == 128 && nx == 160);
+}
+cudaError_t launch_z(int nz, int mode, int lpad, const ZArgs& a, int grid, cudaStream_t s) {
+  switch (nz) {
+    case 16: return launch_z_16(mode, lpad, a, grid, s);
+    case 32: return launch_z_32(mode, lpad, a, grid, s);
+    case 48: return launch_z_48(mode, lpad, a, grid, s);
+    case 64: return launch_z_64(mode, lpad, a, grid, s);
+    case 96: return launch_z_96(mode, lpad, a, grid, s);
+    case 128: return launch_z_128(mode, lpad, a, grid, s);
+    case 160: return launch_z_160(mode, lpad, a, grid, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+cudaError_t launch_xy(int ny, int nx, int mode, int ub, const XYArgs& a, int nz, int ns,
+                      cudaStream_t s) {
+  if (ny == 128 && nx == 160) return launch_xy_128_160(mode, ub, a, nz, ns, s);
+  if (ny != nx) return cudaErrorInvalidValue;
+  switch (nx) {
+    case 16: return launch_xy_16_16(mode, ub, a, nz, ns, s);
+    case 32: return launch_xy_32_32(mode, ub, a, nz, ns, s);
+    case 48: return launch_xy_48_48(mode, ub, a, nz, ns, s);
+    case 64: return launch_xy_64_64(mode, ub, a, nz, ns, s);
+    case 96: return launch_xy_96_96(mode, ub, a, nz, ns, s);
+    case 128: return launch_xy_128_128(mode, ub, a, nz, ns, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+}  // namespace os3d
+
+using namespace os3d;
+
+struct os3d_bank {
+  int dev = 0;
+  int dims[3] = {0, 0, 0};
+  long long nvox = 0;
+  int n_o = 0;
+  os3d_params p{};
+  std::vector<double> orient;          // n_o x 3
+  std::vector<int> slot_a, slot_b;     // orientation pairs (b = -1: unpaired)
+  int block_slots = 1;
+  std::vector<double> b, c;            // Legendre coefficients (L+1 each)
+  HEval h{};
+  int lpad = 16;
+  float* Gs = nullptr;                 // G / n^3
+  float* GM = nullptr;                 // G / (n^3 max(M, eps))
+  float* Minv = nullptr;               // 1 / max(M, eps), 0 outside the ball
+  void* ws = nullptr;                  // default workspace
+  size_t ws_bytes = 0;
+};
+
+namespace {
+
+constexpr double kPi = 3.141592653589793238462643383279502884;
+
+// ---------------------------------------------------------------------------
+// host geometry (FP64)
+// ---------------------------------------------------------------------------
+using V3 = std::array<double, 3>;
+
+V3 normed(const V3& a) {
+  const double n = std::sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
+  return {a[0] / n, a[1] / n, a[2] / n};
+}
+
+void icosahedron(std::vector<V3>& V, std::vector<std::array<int, 3>>& F) {
+  const double phi = (1.0 + std::sqrt(5.0)) / 2.0;
+  V.clear();
+  for (double s1 : {1.0, -1.0})
+    for (double s2 : {1.0, -1.0}) {
+      const V3 a = {0.0, s1, s2 * phi};
+      V.push_back(normed(a));
+      V.push_back(normed({a[1], a[2], a[0]}));
+      V.push_back(normed({a[2], a[0], a[1]}));
+    }
+  // faces: triples of mutually nearest vertices
+  const int n = (int)V.size();
+  auto d2 = [&](int i, int j) {
+    double s = 0;
+    for (int q = 0; q < 3; ++q) s += (V[i][q] - V[j][q]) * (V[i][q] - V[j][q]);
+    return s;
+  };
+  double emin = 1e9;
+  for (int i = 0; i < n; ++i)
+    for (int j = i + 1; j < n; ++j) emin = std::min(emin, d2(i, j));
+  auto adj = [&](int i, int j) { return std::fabs(d2(i, j) - emin) < 1e-9; };
+  F.clear();
+  for (int i = 0; i < n; ++i)
+    for (int j = i + 1; j < n; ++j)
+      for (int k = j + 1; k < n; ++k)
+        if (adj(i, j) && adj(j, k) && adj(i, k)) F.push_back({i, j, k});
+}
+
+void subdivide(std::vector<V3>& V, std::vector<std::array<int, 3>>& F) {
+  std::map<std::pair<int, int>, int> mid;
+  auto m = [&](int a, int b) {
+    const auto key = std::make_pair(std::min(a, b), std::max(a, b));
+    auto it = mid.find(key);
+    if (it != mid.end()) return it->second;
+    V.push_back(normed({V[a][0] + V[b][0], V[a][1] + V[b][1], V[a][2] + V[b][2]}));
+    mid[key] = (int)V.size() - 1;
+    return (int)V.size() - 1;
+  };
+  std::vector<std::array<int, 3>> F2;
+  for (const auto& f : F) {
+    const int ab = m(f[0], f[1]), bc = m(f[1], f[2]), ca = m(f[2], f[0]);
+    F2.push_back({f[0], ab, ca});
+    F2.push_back({ab, f[1], bc});
+    F2.push_back({ca, bc, f[2]});
+    F2.push_back({ab, bc, ca});
+  }
+  F.swap(F2);
+}
+
+// canonical order: representatives by decreasing z then azimuth, then antipodes
+bool canonical_order(const std::vector<V3>& V, std::vector<V3>& out) {
+  constexpr double tol = 1e-9;
+  std::vector<V3> reps;
+  for (const auto& p : V) {
+    const bool rep = p[2] > tol || (std::fabs(p[2]) <= tol &&
+                                    (p[1] > tol || (std::fabs(p[1]) <= tol && p[0] > 0.0)));
+    if (rep) reps.push_back(p);
+  }
+  auto az = [&](const V3& p) {
+    const double a = std::atan2(p[1], p[0]);
+    return a <= -kPi + tol ? kPi : a;
+  };
+  std::stable_sort(reps.begin(), reps.end(), [&](const V3& p, const V3& q) {
+    if (std::fabs(p[2] - q[2]) > tol) return p[2] > q[2];
+    return az(p) < az(q);
+  });
+  if (2 * reps.size() != V.size()) return false;
+  out = reps;
+  for (const auto& p : reps) out.push_back({-p[0], -p[1], -p[2]});
+  return true;
+}
+
+// points of the icosahedron of tessellation order nu (10 nu^2 + 2 points)
+std::vector<V3> tessellation(int nu) {
+  std::vector<V3> V;
+  std::vector<std::array<int, 3>> F;
+  icosahedron(V, F);
+  std::map<std::tuple<long long, long long, long long>, V3> pts;
+  for (const auto& f : F)
+    for (int i = 0; i <= nu; ++i)
+      for (int j = 0; j <= nu - i; ++j) {
+        const int k = nu - i - j;
+        V3 p;
+        for (int q = 0; q < 3; ++q) p[q] = (i * V[f[0]][q] + j * V[f[1]][q] + k * V[f[2]][q]) / nu;
+        p = normed(p);
+        const auto key = std::make_tuple(std::llround(p[0] * 1e9), std::llround(p[1] * 1e9),
+                                         std::llround(p[2] * 1e9));
+        pts[key] = p;
+      }
+  std::vector<V3> out;
+  for (const auto& kv : pts) out.push_back(kv.second);
+  return out;
+}
+
+// Gauss-Legendre nodes/weights on [-1, 1] by Newton's method on P_n
+void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w) {
+  x.assign(n, 0.0);
+  w.assign(n, 0.0);
+  for (int i = 0; i < n; ++i) {
+    double z = std::cos(kPi * (i + 0.75) / (n + 0.5));
+    double dp = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = z;
+      for (int l = 1; l < n; ++l) {
+        const double p2 = ((2 * l + 1) * z * p1 - l * p0) / (l + 1);
+        p0 = p1;
+        p1 = p2;
+      }
+      dp = n * (z * p1 - p0) / (z * z - 1.0);
+      const double dz = p1 / dp;
+      z -= dz;
+      if (std::fabs(dz) < 1e-16) break;
+    }
+    x[i] = z;
+    w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+  }
+}
+
+double legendre_sum(const std::vector<double>& c, double t) {
+  double pm = 1.0, pl = t, s = c[0];
+  const int L = (int)c.size() - 1;
+  if (L >= 1) s += c[1] * t;
+  for (int l = 1; l < L; ++l) {
+    const double pn = ((2 * l + 1) * t * pl - l * pm) / (l + 1);
+    pm = pl;
+    pl = pn;
+    s += c[l + 1] * pn;
+  }
+  return s;
+}
+
+// Chebyshev coefficients a_j of the degree-L polynomial h(t) = sum_l c_l P_l(t):
+// interpolation at the L+1 Chebyshev points is exact for this degree.
+std::vector<double> legendre_to_chebyshev(const std::vector<double>& c) {
+  const int L = (int)c.size() - 1, n = L + 1;
+  std::vector<double> fv(n), a(n, 0.0);
+  for (int j = 0; j < n; ++j) fv[j] = legendre_sum(c, std::cos(kPi * (j + 0.5) / n));
+  for (int m = 0; m < n; ++m) {
+    double s = 0.0;
+    for (int j = 0; j < n; ++j) s += fv[j] * std::cos(kPi * m * (j + 0.5) / n);
+    a[m] = (m == 0 ? 1.0 : 2.0) * s / n;
+  }
+  return a;
+}
+
+bool axis_ok(int n) { return z_supported(n); }
+
+os3d_status check_params(const os3d_params& p) {
+  if (p.k < 0 || p.k > 8 || !(p.s_theta > 0.0) || p.L < 0 || p.L > kMaxL || p.N < 0 || p.N > 64 ||
+      !(p.gamma > 0.0 && p.gamma < 1.0) || !(p.eps > 0.0) || (p.fit_mode != 0 && p.fit_mode != 1) ||
+      p.block_slots < 0 || p.block_slots > kMaxSlots)
+    return OS3D_EINVAL;
+  return OS3D_OK;
+}
+
+struct DevBuf {
+  void* p = nullptr;
+  ~DevBuf() {
+    if (p) cudaFree(p);
+  }
+};
+
+bool fault_is(const char* what) {
+  const char* e = std::getenv("OS3D_FAULT");
+  return e && std::strcmp(e, what) == 0;
+}
+
+// ---------------------------------------------------------------------------
+// diagnostics: launch counter and optional per-kernel CUDA-event timing
+// ---------------------------------------------------------------------------
+std::atomic<unsigned long long> g_launches{0};
+std::atomic<int> g_profile{0};
+std::mutex g_prof_mu;
+struct ProfRec {
+  int kind;
+  cudaEvent_t a, b;
+};
+std::vector<ProfRec> g_prof_pending;
+std::vector<cudaEvent_t> g_event_pool;
+unsigned long long g_prof_launches[OS3D_KIND_COUNT] = {};
+double g_prof_ms[OS3D_KIND_COUNT] = {};
+
+cudaEvent_t take_event() {
+  if (!g_event_pool.empty()) {
+    cudaEvent_t e = g_event_pool.back();
+    g_event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  return e;
+}
+
+template <class F>
+cudaError_t counted_launch(int kind, cudaStream_t s, F&& launch) {
+  cudaEvent_t a = nullptr, b = nullptr;
+  if (g_profile.load()) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    a = take_event();
+    b = take_event();
+    if (a) cudaEventRecord(a, s);
+  }
+  const cudaError_t e = launch();
+  if (e == cudaSuccess) g_launches.fetch_add(1);
+  if (a && b) {
+    cudaEventRecord(b, s);
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    g_prof_pending.push_back({kind, a, b});
+  }
+  return e;
+}
+
+os3d_status current_device_matches(const os3d_bank* b) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return OS3D_ECUDA;
+  return dev == b->dev ? OS3D_OK : OS3D_EINVAL;
+}
+
+}  // namespace
+
+// ===========================================================================
+extern "C" {
+
+const char* os3d_status_string(os3d_status s) {
+  switch (s) {
+    case OS3D_OK: return "ok";
+    case OS3D_EINVAL: return "invalid argument";
+    case OS3D_ENOMEM: return "device allocation failed";
+    case OS3D_ECUDA: return "CUDA error";
+    case OS3D_ETIMEOUT: return "timed out";
+    case OS3D_EUNSUPPORTED: return "unsupported grid size";
+  }
+  return "unknown status";
+}
+
+os3d_status os3d_default_params(os3d_params* p) {
+  if (!p) return OS3D_EINVAL;
+  p->k = 2;
+  p->s_theta = 0.7;
+  p->L = 16;
+  p->N = 8;
+  p->gamma = 0.8;
+  p->eps = 1e-4;
+  p->fit_mode = 1;
+  p->block_slots = 0;
+  return OS3D_OK;
+}
+
+os3d_status os3d_icosa_orientations(int subdiv, double* out, int capacity, int* n_o) {
+  if (subdiv < 0 || subdiv > 4 || !n_o) return OS3D_EINVAL;
+  const int n = 10 * (1 << (2 * subdiv)) + 2;
+  *n_o = n;
+  if (!out || capacity < n) return OS3D_EINVAL;
+  std::vector<V3> V;
+  std::vector<std::array<int, 3>> F;
+  icosahedron(V, F);
+  for (int s = 0; s < subdiv; ++s) subdivide(V, F);
+  std::vector<V3> o;
+  if ((int)V.size() != n || !canonical_order(V, o)) return OS3D_EINVAL;
+  for (int i = 0; i < n; ++i)
+    for (int q = 0; q < 3; ++q) out[3 * i + q] = o[i][q];
+  return OS3D_OK;
+}
+
+os3d_status os3d_make_wavelets(const int dims[3], const double* orient, int n_o,
+                               const os3d_params* pp, void* stream, os3d_bank** out) {
+  if (!dims || !orient || !out || n_o < 1) return OS3D_EINVAL;
+  *out = nullptr;
+  os3d_params p;
+  if (pp) p = *pp;
+  else os3d_default_params(&p);
+  if (check_params(p) != OS3D_OK) return OS3D_EINVAL;
+  for (int i = 0; i < n_o; ++i) {
+    const double* v = orient + 3 * i;
+    const double nn = std::sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+    if (!(std::fabs(nn - 1.0) < 1e-6)) return OS3D_EINVAL;
+  }
+  const int nz = dims[0], ny = dims[1], nx = dims[2];
+  if (nz < 1 || ny < 1 || nx < 1) return OS3D_EINVAL;
+  if (!axis_ok(nz) || !xy_supported(ny, nx) || nx % kTileX) return OS3D_EUNSUPPORTED;
+  if (fault_is("alloc")) return OS3D_ENOMEM;
+  cudaStream_t s = (cudaStream_t)stream;
+
+  os3d_bank* b = new (std::nothrow) os3d_bank();
+  if (!b) return OS3D_ENOMEM;
+  auto fail = [&](os3d_status st) {
+    os3d_destroy_bank(b);
+    return st;
+  };
+  if (cudaGetDevice(&b->dev) != cudaSuccess) return fail(OS3D_ECUDA);
+  b->dims[0] = nz;
+  b->dims[1] = ny;
+  b->dims[2] = nx;
+  b->nvox = (long long)nz * ny * nx;
+  b->n_o = n_o;
+  b->p = p;
+  b->orient.assign(orient, orient + 3 * n_o);
+
+  // antipodal pairs
+  std::vector<int> used(n_o, 0);
+  for (int i = 0; i < n_o; ++i) {
+    if (used[i]) continue;
+    used[i] = 1;
+    int partner = -1;
+    for (int j = 0; j < n_o && partner < 0; ++j) {
+      if (used[j]) continue;
+      double d = 0;
+      for (int q = 0; q < 3; ++q) d = std::max(d, std::fabs(orient[3 * i + q] + orient[3 * j + q]));
+      if (d < 1e-9) partner = j;
+    }
+    if (partner >= 0) used[partner] = 1;
+    b->slot_a.push_back(i);
+    b->slot_b.push_back(partner);
+  }
+  const int nslots = (int)b->slot_a.size();
+  const size_t vol_c64 = sizeof(float2) * (size_t)b->nvox;
+  if (p.block_slots > 0) {
+    b->block_slots = p.block_slots;
+  } else {
+    // keep the per-block intermediates (T) within ~48 MiB of L2
+    long long bs = (48ll << 20) / (long long)vol_c64;
+    b->block_slots = (int)std::max(1ll, std::min<long long>(bs, kMaxSlots));
+  }
+  b->block_slots = std::min(b->block_slots, nslots);
+  b->ws_bytes = vol_c64 * (3 + b->block_slots);
+
+  // device allocations
+  if (cudaMalloc(&b->Gs, sizeof(float) * b->nvox) != cudaSuccess ||
+      cudaMalloc(&b->GM, sizeof(float) * b->nvox) != cudaSuccess ||
+      cudaMalloc(&b->Minv, sizeof(float) * b->nvox) != cudaSuccess ||
+      cudaMalloc(&b->ws, b->ws_bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(OS3D_ENOMEM);
+  }
+
+  // (a1) sample points for the zonal fit
+  std::vector<double> zt, wt;
+  if (p.fit_mode == 1) {
+    for (const auto& q : tessellation(15)) {
+      const double z = std::max(-1.0, std::min(1.0, q[2]));
+      zt.push_back(z);
+      zt.push_back(std::acos(z));
+      wt.push_back(1.0);
+    }
+  } else {
+    std::vector<double> edges = {0.0};
+    std::vector<double> kn;
+    for (int j = 0; j <= p.k + 1; ++j) {
+      const double t = std::fabs(p.s_theta * (j - 0.5 * (p.k + 1)));
+      if (t > 0.0 && t < kPi) kn.push_back(t);
+    }
+    std::sort(kn.begin(), kn.end());
+    kn.erase(std::unique(kn.begin(), kn.end()), kn.end());
+    for (double t : kn) edges.push_back(t);
+    edges.push_back(kPi);
+    std::vector<double> gx, gw;
+    gauss_legendre(64, gx, gw);
+    for (size_t e = 0; e + 1 < edges.size(); ++e) {
+      const double lo = edges[e], hi = edges[e + 1];
+      for (size_t q = 0; q < gx.size(); ++q) {
+        const double th = 0.5 * (hi - lo) * gx[q] + 0.5 * (hi + lo);
+        zt.push_back(std::cos(th));
+        zt.push_back(th);
+        wt.push_back(0.5 * (hi - lo) * gw[q] * std::sin(th));
+      }
+    }
+  }
+  const int npts = (int)wt.size();
+  const int L = p.L;
+  DevBuf dzt, dwt, dout, dc, dslots;
+  if (cudaMalloc(&dzt.p, sizeof(double) * zt.size()) != cudaSuccess ||
+      cudaMalloc(&dwt.p, sizeof(double) * wt.size()) != cudaSuccess ||
+      cudaMalloc(&dout.p, sizeof(double) * 2 * (L + 1)) != cudaSuccess ||
+      cudaMalloc(&dslots.p, sizeof(double) * 4 * nslots) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(OS3D_ENOMEM);
+  }
+  if (cudaMemcpyAsync(dzt.p, zt.data(), sizeof(double) * zt.size(), cudaMemcpyHostToDevice, s) ||
+      cudaMemcpyAsync(dwt.p, wt.data(), sizeof(double) * wt.size(), cudaMemcpyHostToDevice, s))
+    return fail(OS3D_ECUDA);
+  if (launch_fit((const double*)dzt.p, (const double*)dwt.p, npts, p.fit_mode, p.k, p.s_theta, L,
+                 n_o, (double*)dout.p, s) != cudaSuccess)
+    return fail(OS3D_ECUDA);
+  std::vector<double> bc(2 * (L + 1));
+  if (cudaMemcpyAsync(bc.data(), dout.p, sizeof(double) * bc.size(), cudaMemcpyDeviceToHost, s) ||
+      cudaStreamSynchronize(s))
+    return fail(OS3D_ECUDA);
+  b->b.assign(bc.begin(), bc.begin() + L + 1);
+  b->c.assign(bc.begin() + L + 1, bc.end());
+  for (double v : bc)
+    if (!std::isfinite(v)) return fail(OS3D_EINVAL);
+
+  // Chebyshev form for the FP32 transform kernels
+  const std::vector<double> ch = legendre_to_chebyshev(b->c);
+  for (int j = 0; j <= kMaxL; ++j) b->h.a[j] = j <= L ? (float)ch[j] : 0.f;
+  b->h.c0 = (float)b->c[0];
+  b->lpad = L <= 16 ? 16 : 32;
+
+  // (a3) M and the per-voxel factors, FP64
+  std::vector<double> sl(4 * nslots);
+  for (int q = 0; q < nslots; ++q) {
+    for (int d = 0; d < 3; ++d) sl[4 * q + d] = orient[3 * b->slot_a[q] + d];
+    sl[4 * q + 3] = b->slot_b[q] >= 0 ? 1.0 : 0.0;
+  }
+  if (cudaMemcpyAsync(dslots.p, sl.data(), sizeof(double) * sl.size(), cudaMemcpyHostToDevice, s))
+    return fail(OS3D_ECUDA);
+  if (launch_bank_M(nz, ny, nx, p.N, p.gamma, p.eps, (const double*)dout.p + (L + 1), L,
+                    (const double*)dslots.p, nslots, n_o, b->Gs, b->GM, b->Minv, s) != cudaSuccess)
+    return fail(OS3D_ECUDA);
+  // the temporaries are freed when this function returns: wait for the kernels
+  if (cudaStreamSynchronize(s) != cudaSuccess) return fail(OS3D_ECUDA);
+  *out = b;
+  return OS3D_OK;
+}
+
+os3d_status os3d_bank_info(const os3d_bank* b, size_t* ws, size_t* score_bytes) {
+  if (!b) return OS3D_EINVAL;
+  if (ws) *ws = b->ws_bytes;
+  if (score_bytes) *score_bytes = sizeof(float2) * (size_t)b->nvox * b->n_o;
+  return OS3D_OK;
+}
+
+os3d_status os3d_bank_coefficients(const os3d_bank* bk, double* bo, double* co) {
+  if (!bk) return OS3D_EINVAL;
+  if (bo) std::copy(bk->b.begin(), bk->b.end(), bo);
+  if (co) std::copy(bk->c.begin(), bk->c.end(), co);
+  return OS3D_OK;
+}
+
+os3d_status os3d_bank_minv(const os3d_bank* bk, float* minv, void* stream) {
+  if (!bk) return OS3D_EINVAL;
+  if (!minv) return OS3D_OK;
+  if (current_device_matches(bk) != OS3D_OK) return OS3D_EINVAL;
+  if (cudaMemcpyAsync(minv, bk->Minv, sizeof(float) * bk->nvox, cudaMemcpyDeviceToDevice,
+                      (cudaStream_t)stream) != cudaSuccess)
+    return OS3D_ECUDA;
+  return OS3D_OK;
+}
+
+os3d_status os3d_destroy_bank(os3d_bank* b) {
+  if (!b) return OS3D_EINVAL;
+  if (b->Gs) cudaFree(b->Gs);
+  if (b->GM) cudaFree(b->GM);
+  if (b->Minv) cudaFree(b->Minv);
+  if (b->ws) cudaFree(b->ws);
+  delete b;
+  return OS3D_OK;
+}
+
+}  // extern "C"
+
+// ===========================================================================
+// transforms
+// ===========================================================================
+namespace {
+
+struct Work {
+  float2* fh;   // f_hat G / n^3
+  float2* A;    // orientation sum
+  float2* T0;   // per-volume intermediate
+  float2* T;    // block_slots intermediates
+};
+
+Work carve(const os3d_bank* b, void* ws) {
+  float2* base = (float2*)(ws ? ws : b->ws);
+  const long long n = b->nvox;
+  return Work{base, base + n, base + 2 * n, base + 3 * n};
+}
+
+ZArgs zargs_base(const os3d_bank* b) {
+  ZArgs a{};
+  a.ny = b->dims[1];
+  a.nx = b->dims[2];
+  a.wz = float(2.0 * kPi / b->dims[0]);
+  a.wy = float(2.0 * kPi / b->dims[1]);
+  a.wx = float(2.0 * kPi / b->dims[2]);
+  a.slot_stride = b->nvox;
+  a.h = b->h;
+  return a;
+}
+
+XYArgs xyargs_one(const void* in, long long ia, void* out, long long oa) {
+  XYArgs a{};
+  a.in = in;
+  a.out = out;
+  a.in_a[0] = ia;
+  a.in_b[0] = -1;
+  a.out_a[0] = oa;
+  a.out_b[0] = -1;
+  return a;
+}
+
+os3d_status check_call(const os3d_bank* b, const void* x, const void* y, int batch, int udtype,
+                       void* ws) {
+  if (!b || !x || !y || batch < 1) return OS3D_EINVAL;
+  if (udtype != OS3D_U_C64 && udtype != OS3D_U_BF16X2) return OS3D_EINVAL;
+  if (ws && (reinterpret_cast<uintptr_t>(ws) & 255)) return OS3D_EINVAL;
+  return current_device_matches(b);
+}
+
+#define OS3D_CK(call)                         \
+  do {                                        \
+    if ((call) != cudaSuccess) return OS3D_ECUDA; \
+  } while (0)
+
+// inverse (use_m = true) or adjoint (use_m = false)
+os3d_status backward_impl(const os3d_bank* b, const void* U, int udtype, int batch, float* fout,
+                          void* ws, cudaStream_t s, bool use_m) {
+  const Work w = carve(b, ws);
+  const int nz = b->dims[0], ny = b->dims[1], nx = b->dims[2];
+  const int nslots = (int)b->slot_a.size();
+  const int ztiles = ny * (nx / kTileX);
+  const long long n = b->nvox;
+  for (int v = 0; v < batch; ++v) {
+    int q = 0;
+    for (int s0 = 0; s0 < nslots; s0 += b->block_slots, ++q) {
+      const int ns = std::min(b->block_slots, nslots - s0);
+      XYArgs xa{};
+      xa.in = U;
+      xa.out = w.T;
+      ZArgs za = zargs_base(b);
+      za.in = w.T;
+      za.out = w.A;
+      za.nslots = ns;
+      za.accumulate = q > 0;
+      for (int j = 0; j < ns; ++j) {
+        const int ia = b->slot_a[s0 + j], ib = b->slot_b[s0 + j];
+        xa.in_a[j] = ((long long)v * b->n_o + ia) * n;
+        xa.in_b[j] = ib >= 0 ? ((long long)v * b->n_o + ib) * n : -1;
+        xa.out_a[j] = (long long)j * n;
+        xa.out_b[j] = -1;
+        for (int d = 0; d < 3; ++d) za.nvec[j][d] = (float)b->orient[3 * ia + d];
+      }
+      OS3D_CK(counted_launch(OS3D_KIND_XY_INV_SCORE, s, [&] { return launch_xy(ny, nx, XY_INV_SCORE, udtype, xa, nz, ns, s); }));
+      OS3D_CK(counted_launch(OS3D_KIND_Z_INV_SCORE, s, [&] { return launch_z(nz, Z_INV_SCORE, b->lpad, za, ztiles, s); }));
+    }
+    ZArgs zf = zargs_base(b);
+    zf.in = w.A;
+    zf.out = w.T0;
+    zf.mult = use_m ? b->GM : b->Gs;
+    OS3D_CK(counted_launch(OS3D_KIND_Z_INV_FINAL, s, [&] { return launch_z(nz, Z_INV_FINAL, b->lpad, zf, ztiles, s); }));
+    const XYArgs xf = xyargs_one(w.T0, 0, fout, (long long)v * n);
+    OS3D_CK(counted_launch(OS3D_KIND_XY_INV_REAL, s, [&] { return launch_xy(ny, nx, XY_INV_REAL, 0, xf, nz, 1, s); }));
+  }
+  return OS3D_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+os3d_status os3d_forward(const os3d_bank* b, const float* f, int batch, void* U,
+                         os3d_udtype udtype, void* ws, void* stream) {
+  const os3d_status st = check_call(b, f, U, batch, udtype, ws);
+  if (st != OS3D_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  const Work w = carve(b, ws);
+  const int nz = b->dims[0], ny = b->dims[1], nx = b->dims[2];
+  const int nslots = (int)b->slot_a.size();
+  const int ztiles = ny * (nx / kTileX);
+  const long long n = b->nvox;
+  for (int v = 0; v < batch; ++v) {
+    // (a4) f_hat G / n^3
+    const XYArgs x0 = xyargs_one(f, (long long)v * n, w.T0, 0);
+    OS3D_CK(counted_launch(OS3D_KIND_XY_FWD_REAL, s, [&] { return launch_xy(ny, nx, XY_FWD_REAL, 0, x0, nz, 1, s); }));
+    ZArgs zp = zargs_base(b);
+    zp.in = w.T0;
+    zp.out = w.fh;
+    zp.mult = b->Gs;
+    OS3D_CK(counted_launch(OS3D_KIND_Z_FWD_PREP, s, [&] { return launch_z(nz, Z_FWD_PREP, b->lpad, zp, ztiles, s); }));
+    // (a5) per block of orientation pairs
+    for (int s0 = 0; s0 < nslots; s0 += b->block_slots) {
+      const int ns = std::min(b->block_slots, nslots - s0);
+      ZArgs za = zargs_base(b);
+      za.in = w.fh;
+      za.out = w.T;
+      za.nslots = ns;
+      XYArgs xa{};
+      xa.in = w.T;
+      xa.out = U;
+      for (int j = 0; j < ns; ++j) {
+        const int ia = b->slot_a[s0 + j], ib = b->slot_b[s0 + j];
+        for (int d = 0; d < 3; ++d) za.nvec[j][d] = (float)b->orient[3 * ia + d];
+        xa.in_a[j] = (long long)j * n;
+        xa.in_b[j] = -1;
+        xa.out_a[j] = ((long long)v * b->n_o + ia) * n;
+        xa.out_b[j] = ib >= 0 ? ((long long)v * b->n_o + ib) * n : -1;
+      }
+      OS3D_CK(counted_launch(OS3D_KIND_Z_FWD_SCORE, s, [&] { return launch_z(nz, Z_FWD_SCORE, b->lpad, za, ztiles, s); }));
+      OS3D_CK(counted_launch(OS3D_KIND_XY_FWD_SCORE, s, [&] { return launch_xy(ny, nx, XY_FWD_SCORE, udtype, xa, nz, ns, s); }));
+    }
+  }
+  return OS3D_OK;
+}
+
+os3d_status os3d_inverse(const os3d_bank* b, const void* U, os3d_udtype udtype, int batch,
+                         float* f_out, void* ws, void* stream) {
+  const os3d_status st = check_call(b, U, f_out, batch, udtype, ws);
+  if (st != OS3D_OK) return st;
+  return backward_impl(b, U, udtype, batch, f_out, ws, (cudaStream_t)stream, true);
+}
+
+os3d_status os3d_adjoint(const os3d_bank* b, const void* G, os3d_udtype udtype, int batch,
+                         float* grad_f, void* ws, void* stream) {
+  const os3d_status st = check_call(b, G, grad_f, batch, udtype, ws);
+  if (st != OS3D_OK) return st;
+  return backward_impl(b, G, udtype, batch, grad_f, ws, (cudaStream_t)stream, false);
+}
+
+}  // extern "C"
+
+extern "C" {
+
+unsigned long long os3d_launch_count(void) { return g_launches.load(); }
+
+os3d_status os3d_profile_enable(int on) {
+  g_profile.store(on ? 1 : 0);
+  return OS3D_OK;
+}
+
+os3d_status os3d_profile_read(int kind, unsigned long long* launches, double* ms) {
+  if (kind < 0 || kind >= OS3D_KIND_COUNT) return OS3D_EINVAL;
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  for (const auto& r : g_prof_pending) {
+    float t = 0.f;
+    if (cudaEventSynchronize(r.b) != cudaSuccess || cudaEventElapsedTime(&t, r.a, r.b) != cudaSuccess)
+      return OS3D_ECUDA;
+    g_prof_launches[r.kind] += 1;
+    g_prof_ms[r.kind] += t;
+    g_event_pool.push_back(r.a);
+    g_event_pool.push_back(r.b);
+  }
+  g_prof_pending.clear();
+  if (launches) *launches = g_prof_launches[kind];
+  if (ms) *ms = g_prof_ms[kind];
+  return OS3D_OK;
+}
+
+os3d_status os3d_profile_reset(void) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  for (int k = 0; k < OS3D_KIND_COUNT; ++k) {
+    g_prof_launches[k] = 0;
+    g_prof_ms[k] = 0.0;
+  }
+  for (const auto& r : g_prof_pending) {
+    cudaEventSynchronize(r.b);
+    g_event_pool.push_back(r.a);
+    g_event_pool.push_back(r.b);
+  }
+  g_prof_pending.clear();
+  return OS3D_OK;
+}
+
+const char* os3d_kernel_kind_name(int kind) {
+  static const char* names[OS3D_KIND_COUNT] = {"xy_fwd_real", "xy_fwd_score", "xy_inv_score",
+                                                "xy_inv_real", "z_fwd_prep", "z_fwd_score",
+                                                "z_inv_score", "z_inv_final"};
+  return (kind >= 0 && kind < OS3D_KIND_COUNT) ? names[kind] : "unknown";
+}
+
+}  // extern "C"

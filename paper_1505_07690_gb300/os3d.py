@@ -1,0 +1,269 @@
+"""Python binding of libos3d (include/os3d.h): argument marshalling only.
+
+Every function here has the name of the C entry point it calls. Device
+memory comes from torch tensors, streams from torch's current stream; all
+arithmetic runs in the library's CUDA kernels. There is no fallback: if the
+library is not built, or no CUDA device is present, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libos3d.so")
+
+OS3D_U_C64 = 0
+OS3D_U_BF16X2 = 1
+_STATUS = {0: "OS3D_OK", 1: "OS3D_EINVAL", 2: "OS3D_ENOMEM", 3: "OS3D_ECUDA",
+           4: "OS3D_ETIMEOUT", 5: "OS3D_EUNSUPPORTED"}
+
+
+class os3d_params(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_int), ("s_theta", ctypes.c_double), ("L", ctypes.c_int),
+                ("N", ctypes.c_int), ("gamma", ctypes.c_double), ("eps", ctypes.c_double),
+                ("fit_mode", ctypes.c_int), ("block_slots", ctypes.c_int)]
+
+
+class OS3DError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        super().__init__(f"{where}: {_STATUS.get(status, status)} "
+                         f"({lib().os3d_status_string(status).decode()})")
+
+
+_lib = None
+
+
+def lib():
+    """The loaded libos3d.so (ctypes)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is not built; run paper_1505_07690_gb300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+        L.os3d_status_string.restype = ctypes.c_char_p
+        L.os3d_status_string.argtypes = [i]
+        L.os3d_default_params.argtypes = [ctypes.POINTER(os3d_params)]
+        L.os3d_icosa_orientations.argtypes = [i, ctypes.POINTER(d), i, ctypes.POINTER(i)]
+        L.os3d_make_wavelets.argtypes = [ctypes.POINTER(i), ctypes.POINTER(d), i,
+                                         ctypes.POINTER(os3d_params), vp, ctypes.POINTER(vp)]
+        L.os3d_forward.argtypes = [vp, vp, i, vp, i, vp, vp]
+        L.os3d_inverse.argtypes = [vp, vp, i, i, vp, vp, vp]
+        L.os3d_adjoint.argtypes = [vp, vp, i, i, vp, vp, vp]
+        L.os3d_bank_info.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t),
+                                     ctypes.POINTER(ctypes.c_size_t)]
+        L.os3d_bank_coefficients.argtypes = [vp, ctypes.POINTER(d), ctypes.POINTER(d)]
+        L.os3d_bank_minv.argtypes = [vp, vp, vp]
+        L.os3d_destroy_bank.argtypes = [vp]
+        L.os3d_launch_count.restype = ctypes.c_ulonglong
+        L.os3d_launch_count.argtypes = []
+        L.os3d_profile_enable.argtypes = [i]
+        L.os3d_profile_read.argtypes = [i, ctypes.POINTER(ctypes.c_ulonglong), ctypes.POINTER(d)]
+        L.os3d_profile_reset.argtypes = []
+        L.os3d_kernel_kind_name.restype = ctypes.c_char_p
+        L.os3d_kernel_kind_name.argtypes = [i]
+        for name in ("os3d_default_params", "os3d_icosa_orientations", "os3d_make_wavelets",
+                     "os3d_forward", "os3d_inverse", "os3d_adjoint", "os3d_bank_info",
+                     "os3d_bank_coefficients", "os3d_bank_minv", "os3d_destroy_bank",
+                     "os3d_profile_enable", "os3d_profile_read", "os3d_profile_reset"):
+            getattr(L, name).restype = i
+        _lib = L
+    return _lib
+
+
+def _check(status, where):
+    if status != 0:
+        raise OS3DError(status, where)
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, torch.cuda.Stream):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def os3d_default_params(**overrides) -> os3d_params:
+    p = os3d_params()
+    _check(lib().os3d_default_params(ctypes.byref(p)), "os3d_default_params")
+    for k, v in overrides.items():
+        setattr(p, k, v)
+    return p
+
+
+def os3d_icosa_orientations(subdiv: int) -> np.ndarray:
+    n = ctypes.c_int(0)
+    lib().os3d_icosa_orientations(int(subdiv), None, 0, ctypes.byref(n))
+    if n.value <= 0:
+        raise OS3DError(1, "os3d_icosa_orientations")
+    out = np.zeros((n.value, 3), dtype=np.float64)
+    _check(lib().os3d_icosa_orientations(int(subdiv), out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                         n.value, ctypes.byref(n)), "os3d_icosa_orientations")
+    return out
+
+
+class Bank:
+    """Handle of a library-owned wavelet bank (os3d_bank*)."""
+
+    def __init__(self, handle, dims, n_o, params):
+        self.handle = handle
+        self.dims = tuple(dims)
+        self.n_o = n_o
+        self.params = params
+        ws, sb = ctypes.c_size_t(0), ctypes.c_size_t(0)
+        _check(lib().os3d_bank_info(handle, ctypes.byref(ws), ctypes.byref(sb)), "os3d_bank_info")
+        self.workspace_bytes = ws.value
+        self.score_bytes = sb.value
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h and _lib is not None:
+            _lib.os3d_destroy_bank(h)
+            self.handle = None
+
+
+def os3d_make_wavelets(dims, orient, params: os3d_params | None = None, stream=None) -> Bank:
+    dims_c = (ctypes.c_int * 3)(*[int(d) for d in dims])
+    o = np.ascontiguousarray(np.asarray(orient, dtype=np.float64).reshape(-1, 3))
+    p = params if params is not None else os3d_default_params()
+    h = ctypes.c_void_p(0)
+    _check(lib().os3d_make_wavelets(dims_c, o.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                    len(o), ctypes.byref(p), _stream(stream), ctypes.byref(h)),
+           "os3d_make_wavelets")
+    return Bank(h, dims, len(o), p)
+
+
+def os3d_destroy_bank(bank: Bank):
+    if bank.handle:
+        _check(lib().os3d_destroy_bank(bank.handle), "os3d_destroy_bank")
+        bank.handle = None
+
+
+def os3d_bank_coefficients(bank: Bank):
+    L = bank.params.L
+    b = np.zeros(L + 1)
+    c = np.zeros(L + 1)
+    dp = ctypes.POINTER(ctypes.c_double)
+    _check(lib().os3d_bank_coefficients(bank.handle, b.ctypes.data_as(dp), c.ctypes.data_as(dp)),
+           "os3d_bank_coefficients")
+    return b, c
+
+
+def os3d_bank_minv(bank: Bank, stream=None):
+    import torch
+    out = torch.empty(bank.dims, dtype=torch.float32, device="cuda")
+    _check(lib().os3d_bank_minv(bank.handle, _ptr(out), _stream(stream)), "os3d_bank_minv")
+    return out
+
+
+def _udtype(U):
+    import torch
+    if U.dtype == torch.complex64:
+        return OS3D_U_C64
+    if U.dtype == torch.bfloat16 and U.shape[-1] == 2:
+        return OS3D_U_BF16X2
+    raise TypeError("U must be complex64, or bfloat16 with a trailing (re, im) axis of 2")
+
+
+def _batch_of(x, nd, dims):
+    if tuple(x.shape[-nd:]) != tuple(dims):
+        raise ValueError(f"shape {tuple(x.shape)} does not end with {tuple(dims)}")
+    return int(np.prod(x.shape[:-nd])) if x.dim() > nd else 1
+
+
+def new_score(bank: Bank, batch: int, bf16: bool = False):
+    import torch
+    shape = (batch, bank.n_o) + bank.dims
+    if bf16:
+        return torch.empty(shape + (2,), dtype=torch.bfloat16, device="cuda")
+    return torch.empty(shape, dtype=torch.complex64, device="cuda")
+
+
+def _check_score(bank, U):
+    if not (U.is_cuda and U.is_contiguous()):
+        raise ValueError("U must be a contiguous CUDA tensor")
+    ud = _udtype(U)
+    core = U.shape[:-1] if ud == OS3D_U_BF16X2 else U.shape
+    if tuple(core[-4:]) != (bank.n_o,) + bank.dims:
+        raise ValueError(f"score shape {tuple(U.shape)} does not match the bank")
+    batch = int(np.prod(core[:-4])) if len(core) > 4 else 1
+    return ud, batch
+
+
+def _ws_ptr(workspace):
+    return ctypes.c_void_p(0) if workspace is None else _ptr(workspace)
+
+
+def os3d_forward(bank: Bank, f, U=None, bf16: bool = False, workspace=None, stream=None):
+    """U = W f (Eq. construction1Discrete) for real float32 volumes f."""
+    import torch
+    if not (f.is_cuda and f.dtype == torch.float32 and f.is_contiguous()):
+        raise ValueError("f must be a contiguous float32 CUDA tensor")
+    batch = _batch_of(f, 3, bank.dims)
+    if U is None:
+        U = new_score(bank, batch, bf16)
+    ud, ub = _check_score(bank, U)
+    if ub != batch:
+        raise ValueError("batch of U and f differ")
+    _check(lib().os3d_forward(bank.handle, _ptr(f), batch, _ptr(U), ud, _ws_ptr(workspace),
+                              _stream(stream)), "os3d_forward")
+    return U
+
+
+def _backward(fn, name, bank, U, out, workspace, stream):
+    import torch
+    ud, batch = _check_score(bank, U)
+    if out is None:
+        out = torch.empty((batch,) + bank.dims, dtype=torch.float32, device="cuda")
+    if not (out.is_cuda and out.dtype == torch.float32 and out.is_contiguous()
+            and out.numel() == batch * int(np.prod(bank.dims))):
+        raise ValueError("output must be a contiguous float32 CUDA tensor of the batch's size")
+    _check(fn(bank.handle, _ptr(U), ud, batch, _ptr(out), _ws_ptr(workspace), _stream(stream)), name)
+    return out
+
+
+def os3d_inverse(bank: Bank, U, f_out=None, workspace=None, stream=None):
+    """Exact inverse (Eq. Reconstruction1Discrete, Sec. 3.1 clamp)."""
+    return _backward(lib().os3d_inverse, "os3d_inverse", bank, U, f_out, workspace, stream)
+
+
+def os3d_adjoint(bank: Bank, G, grad_f=None, workspace=None, stream=None):
+    """Re W^* G: the gradient with respect to a real image."""
+    return _backward(lib().os3d_adjoint, "os3d_adjoint", bank, G, grad_f, workspace, stream)
+
+
+OS3D_KIND_COUNT = 8
+
+
+def os3d_launch_count() -> int:
+    """Kernels launched by the library so far in this process."""
+    return int(lib().os3d_launch_count())
+
+
+def os3d_profile_enable(on: bool = True):
+    _check(lib().os3d_profile_enable(1 if on else 0), "os3d_profile_enable")
+
+
+def os3d_profile_reset():
+    _check(lib().os3d_profile_reset(), "os3d_profile_reset")
+
+
+def os3d_profile_read():
+    """{kernel kind name: (launches, total ms)} since the last reset."""
+    out = {}
+    for k in range(OS3D_KIND_COUNT):
+        n = ctypes.c_ulonglong(0)
+        ms = ctypes.c_double(0.0)
+        _check(lib().os3d_profile_read(k, ctypes.byref(n), ctypes.byref(ms)), "os3d_profile_read")
+        out[lib().os3d_kernel_kind_name(k).decode()] = (int(n.value), float(ms.value))
+    return out

@@ -1,0 +1,97 @@
+"""CPU checks of the C-ABI library: it builds, loads, exports what the header
+declares, and its host-only logic (orientation sets, argument checks)
+matches the oracle. No CUDA compute call is made here."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import os3d_oracle as O
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_1505_07690_gb300 import build, os3d
+    build.build()
+    return os3d.lib()
+
+
+def test_exports_every_declared_symbol(L):
+    hdr = open(os.path.join(ROOT, "include", "os3d.h")).read()
+    names = set(re.findall(r"\b(os3d_[a-z_0-9]+)\s*\(", hdr))
+    assert len(names) >= 11
+    for n in names:
+        assert hasattr(L, n), n
+
+
+def test_orientations_match_oracle(L):
+    from paper_1505_07690_gb300 import os3d
+    for s in (0, 1, 2, 3):
+        a = os3d.os3d_icosa_orientations(s)
+        b = O.icosa_orientations(s)
+        assert a.shape == b.shape
+        assert np.abs(a - b).max() < 1e-12
+
+
+def test_orientation_capacity_and_range(L):
+    n = ctypes.c_int(0)
+    buf = (ctypes.c_double * 30)()
+    assert L.os3d_icosa_orientations(1, buf, 10, ctypes.byref(n)) == 1   # EINVAL
+    assert n.value == 42
+    assert L.os3d_icosa_orientations(7, buf, 10, ctypes.byref(n)) == 1
+
+
+def test_default_params_and_status_strings(L):
+    from paper_1505_07690_gb300 import os3d
+    p = os3d.os3d_default_params()
+    assert (p.k, p.s_theta, p.L, p.N, p.gamma, p.eps, p.fit_mode) == (2, 0.7, 16, 8, 0.8, 1e-4, 1)
+    for s in range(6):
+        assert len(L.os3d_status_string(s)) > 0
+
+
+def test_argument_errors_before_any_launch(L):
+    from paper_1505_07690_gb300 import os3d
+    p = os3d.os3d_default_params()
+    V = O.icosa_orientations(1)
+    Vp = V.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    h = ctypes.c_void_p(0)
+    dims = (ctypes.c_int * 3)(32, 32, 32)
+    # NULL orientation pointer, n_o < 1
+    assert L.os3d_make_wavelets(dims, None, 42, ctypes.byref(p), None, ctypes.byref(h)) == 1
+    assert L.os3d_make_wavelets(dims, Vp, 0, ctypes.byref(p), None, ctypes.byref(h)) == 1
+    # non-unit orientation
+    bad = V.copy(); bad[3] *= 1.01
+    assert L.os3d_make_wavelets(dims, bad.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), 42,
+                                ctypes.byref(p), None, ctypes.byref(h)) == 1
+    # parameters out of range
+    for field, val in (("L", 33), ("eps", 0.0), ("gamma", 1.0), ("k", 9), ("fit_mode", 2),
+                       ("s_theta", -1.0), ("block_slots", 9)):
+        q = os3d.os3d_default_params(**{field: val})
+        assert L.os3d_make_wavelets(dims, Vp, 42, ctypes.byref(q), None, ctypes.byref(h)) == 1, field
+    # grid without a compiled plan
+    for d in ((30, 32, 32), (32, 32, 40), (256, 256, 256), (32, 64, 96)):
+        dd = (ctypes.c_int * 3)(*d)
+        st = L.os3d_make_wavelets(dd, Vp, 42, ctypes.byref(p), None, ctypes.byref(h))
+        assert st == 5, d
+    # transform calls on a NULL bank
+    assert L.os3d_forward(None, None, 1, None, 0, None, None) == 1
+    assert L.os3d_inverse(None, None, 0, 1, None, None, None) == 1
+    assert L.os3d_adjoint(None, None, 0, 1, None, None, None) == 1
+    assert L.os3d_bank_info(None, None, None) == 1
+    assert L.os3d_destroy_bank(None) == 1
+
+
+def test_injected_allocation_failure(L, monkeypatch):
+    from paper_1505_07690_gb300 import os3d
+    p = os3d.os3d_default_params()
+    V = O.icosa_orientations(1)
+    h = ctypes.c_void_p(0)
+    dims = (ctypes.c_int * 3)(32, 32, 32)
+    monkeypatch.setenv("OS3D_FAULT", "alloc")
+    st = L.os3d_make_wavelets(dims, V.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), 42,
+                              ctypes.byref(p), None, ctypes.byref(h))
+    assert st == 2 and not h.value

@@ -1,0 +1,197 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle on the
+same seeded inputs. Tolerance: relative L2 error <= 1e-5 for FP32 results
+(complex64 scores, reconstructions, adjoints); BF16-stored scores <= 5e-3."""
+import numpy as np
+import pytest
+
+from oracle import os3d_oracle as O
+from paper_1505_07690_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+TOL_BF16 = 5e-3
+
+
+def rel(a, b):
+    a = np.asarray(a)
+    b = np.asarray(b)
+    return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
+
+
+@pytest.fixture(scope="module")
+def M():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1505_07690_gb300 import build, os3d
+    build.build()
+    return os3d
+
+
+def _params(M, **kw):
+    p = M.os3d_default_params()
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+def _oracle_params(p):
+    return O.Params(k=p.k, s_theta=p.s_theta, L=p.L, N=p.N, gamma=p.gamma, eps=p.eps,
+                    fit_mode=p.fit_mode)
+
+
+def _pair(M, dims, subdiv=1, orient=None, **kw):
+    p = _params(M, **kw)
+    Vg = M.os3d_icosa_orientations(subdiv) if orient is None else orient
+    Vo = O.icosa_orientations(subdiv) if orient is None else orient
+    bank = M.os3d_make_wavelets(dims, Vg, p)
+    ob = O.Bank(dims, Vo, _oracle_params(p))
+    return bank, ob
+
+
+def _to_np(t):
+    import torch
+    torch.cuda.synchronize()
+    return t.detach().cpu().numpy()
+
+
+def _cuda(x):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+@pytest.mark.parametrize("fit_mode,L", [(1, 12), (0, 16), (1, 20)])
+def test_coefficients_fp64(M, fit_mode, L):
+    bank, ob = _pair(M, (16, 16, 16), fit_mode=fit_mode, L=L)
+    b, c = M.os3d_bank_coefficients(bank)
+    bo = O.fit_coefficients(ob.p)
+    assert np.abs(b - bo).max() <= 1e-10 * np.abs(bo).max()
+    assert np.abs(c - ob.c).max() <= 1e-10 * np.abs(ob.c).max()
+
+
+def test_minv_fp64(M):
+    bank, ob = _pair(M, (32, 32, 32), L=12)
+    mi = _to_np(M.os3d_bank_minv(bank))
+    assert rel(mi, ob.M_inv()) < 1e-6
+
+
+def _check_forward_inverse(M, dims, f, subdiv=1, orient=None, batch_oracle=True, **kw):
+    bank, ob = _pair(M, dims, subdiv, orient, **kw)
+    U = M.os3d_forward(bank, _cuda(f))
+    Ug = _to_np(U)[0]
+    Uo = O.forward(f, ob)
+    assert rel(Ug, Uo) <= TOL
+    fr = _to_np(M.os3d_inverse(bank, U))[0]
+    fro = O.inverse(Uo, ob)
+    assert rel(fr, fro) <= TOL
+    return bank, ob, Uo
+
+
+def test_forward_inverse_tubes32_no42(M):
+    """32^3 straight-tube volume, 42 orientations, L = 12 (the parity workload)."""
+    f = synth.workload_volume("tubes32_no42")
+    _check_forward_inverse(M, (32, 32, 32), f, L=12)
+
+
+@pytest.mark.parametrize("dims,subdiv,L,bs", [((16, 16, 16), 0, 8, 0), ((16, 16, 16), 1, 16, 4),
+                                              ((48, 48, 48), 1, 16, 0), ((32, 32, 32), 2, 16, 3),
+                                              ((64, 64, 64), 0, 16, 0)])
+def test_forward_inverse_sizes(M, dims, subdiv, L, bs):
+    f = synth.straight_tubes(dims, 2, seed=3, noise=0.1)
+    _check_forward_inverse(M, dims, f, subdiv=subdiv, L=L, block_slots=bs)
+
+
+def test_unpaired_orientations_and_ragged_blocks(M):
+    """Orientations without antipodes take the single-orientation path; 21
+    slots in blocks of 4 leave a ragged last block."""
+    V = O.icosa_orientations(1)[:21].copy()
+    f = synth.straight_tubes((32, 32, 32), 3, seed=4)
+    _check_forward_inverse(M, (32, 32, 32), f, orient=V, L=12, block_slots=4)
+
+
+def test_inverse_and_adjoint_of_arbitrary_scores(M):
+    """Inputs that are not scores of any image: exercises the pair folding
+    U_a + conj(U_b) for general U."""
+    dims = (32, 32, 32)
+    bank, ob = _pair(M, dims, L=12)
+    rng = np.random.default_rng(7)
+    G = (rng.standard_normal((1, 42) + dims) + 1j * rng.standard_normal((1, 42) + dims)).astype(np.complex64)
+    Gd = _cuda(G)
+    fr = _to_np(M.os3d_inverse(bank, Gd))[0]
+    assert rel(fr, O.inverse(G[0].astype(np.complex128), ob)) <= TOL
+    ga = _to_np(M.os3d_adjoint(bank, Gd))[0]
+    assert rel(ga, O.adjoint(G[0].astype(np.complex128), ob)) <= TOL
+
+
+def test_batch_of_two(M):
+    dims = (32, 32, 32)
+    bank, ob = _pair(M, dims, L=12)
+    f = np.stack([synth.straight_tubes(dims, 3, seed=s) for s in (11, 12)])
+    U = M.os3d_forward(bank, _cuda(f))
+    Ug = _to_np(U)
+    fr = _to_np(M.os3d_inverse(bank, U))
+    for b in range(2):
+        Uo = O.forward(f[b], ob)
+        assert rel(Ug[b], Uo) <= TOL
+        assert rel(fr[b], O.inverse(Uo, ob)) <= TOL
+
+
+def test_bf16_storage(M):
+    import torch
+    dims = (32, 32, 32)
+    bank, ob = _pair(M, dims, L=12)
+    f = synth.workload_volume("tubes32_no42")
+    Ub = M.os3d_forward(bank, _cuda(f), bf16=True)
+    assert Ub.dtype == torch.bfloat16 and Ub.shape[-1] == 2
+    Ug = _to_np(Ub.float())[0]
+    Ug = Ug[..., 0] + 1j * Ug[..., 1]
+    Uo = O.forward(f, ob)
+    assert rel(Ug, Uo) <= TOL_BF16
+    fr = _to_np(M.os3d_inverse(bank, Ub))[0]
+    assert rel(fr, O.inverse(Uo, ob)) <= TOL_BF16
+
+
+def test_clamp_and_edge_parameters(M):
+    """N = 20 (the figures' radial order): the eps clamp binds near rho_N."""
+    dims = (32, 32, 32)
+    f = synth.straight_tubes(dims, 3, seed=5)
+    _check_forward_inverse(M, dims, f, L=16, N=20, gamma=0.85, s_theta=0.7)
+    # eps above max M: the inverse equals the adjoint / eps
+    bank, ob = _pair(M, dims, L=12, eps=50.0)
+    U = M.os3d_forward(bank, _cuda(f))
+    fi = _to_np(M.os3d_inverse(bank, U))[0]
+    fa = _to_np(M.os3d_adjoint(bank, U))[0]
+    assert rel(fi, fa / 50.0) <= TOL
+
+
+def test_workspace_argument(M):
+    import torch
+    dims = (32, 32, 32)
+    bank, ob = _pair(M, dims, L=12)
+    f = synth.straight_tubes(dims, 3, seed=6)
+    ws = torch.empty(bank.workspace_bytes, dtype=torch.uint8, device="cuda")
+    U = M.os3d_forward(bank, _cuda(f), workspace=ws)
+    Uo = O.forward(f, ob)
+    assert rel(_to_np(U)[0], Uo) <= TOL
+    fr = _to_np(M.os3d_inverse(bank, U, workspace=ws))[0]
+    assert rel(fr, O.inverse(Uo, ob)) <= TOL
+
+
+def test_headline_size_sampled(M):
+    """128^3 spline tubes, 162 orientations, L = 16, in the benchmark's
+    configuration: sampled orientations against the oracle one by one, and
+    the reconstruction against the exactly known W^-1 W f = IDFT[1_ball f_hat]."""
+    dims = (128, 128, 128)
+    f = synth.workload_volume("splines128_no162")
+    bank, ob = _pair(M, dims, subdiv=2, L=16)
+    U = M.os3d_forward(bank, _cuda(f))
+    fhat = np.fft.fftn(f.astype(np.float64))
+    for i in (0, 37, 80, 81, 161):
+        Ui = _to_np(U[0, i])
+        assert rel(Ui, O.forward_one(fhat, ob, i)) <= TOL, i
+    fr = _to_np(M.os3d_inverse(bank, U))[0]
+    wz, wy, wx = O.freq_grid(dims)
+    ball = np.sqrt(wz ** 2 + wy ** 2 + wx ** 2) < np.pi
+    fb = np.fft.ifftn(fhat * ball).real
+    assert rel(fr, fb) <= TOL
