@@ -43,6 +43,8 @@ def _args():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--bf16", action="store_true", help="store U as bfloat16 pairs")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default=WORKLOAD,
+                    help="named synthetic workload (default: the 128^3 x 162 headline)")
     return ap.parse_args()
 
 
@@ -360,7 +362,9 @@ def run_ours(args):
 
 
 def main():
+    global WORKLOAD
     args = _args()
+    WORKLOAD = args.workload
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

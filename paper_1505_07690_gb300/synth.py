@@ -102,6 +102,8 @@ WORKLOADS = {
                          subdiv=1, L=12),
     "splines128_no162": dict(shape=(128, 128, 128), kind="spline", n_tubes=12, noise=0.2,
                              subdiv=2, L=16),
+    "splines128_no42": dict(shape=(128, 128, 128), kind="spline", n_tubes=12, noise=0.2,
+                            subdiv=1, L=16),
     "splines256_no42": dict(shape=(256, 256, 256), kind="spline", n_tubes=40, noise=0.2,
                             subdiv=1, L=20),
     "splines96x8_no42": dict(shape=(96, 96, 96), kind="spline", n_tubes=12, noise=0.2,
