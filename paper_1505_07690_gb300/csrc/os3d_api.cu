@@ -75,7 +75,7 @@ struct os3d_bank {
   int block_slots = 1;
   std::vector<double> b, c;            // Legendre coefficients (L+1 each)
   HEval h{};
-  int lpad = 16;
+  int ev = 0;                          // wavelet evaluation form (see HEval)
   float* Gs = nullptr;                 // G / n^3
   float* GM = nullptr;                 // G / (n^3 max(M, eps))
   float* Minv = nullptr;               // 1 / max(M, eps), 0 outside the ball
@@ -240,6 +240,48 @@ std::vector<double> legendre_to_chebyshev(const std::vector<double>& c) {
     a[m] = (m == 0 ? 1.0 : 2.0) * s / n;
   }
   return a;
+}
+
+// h(t) = sum_l c_l P_l(t) = E(v) + t O(v) with v = t^2 - 1/2: monomial
+// coefficients of h (Legendre recurrence on coefficient vectors), split into
+// even and odd parts, then re-centred from s = t^2 to v = s - 1/2.
+void split_monomial(const std::vector<double>& c, std::vector<double>& e, std::vector<double>& o) {
+  const int L = (int)c.size() - 1;
+  std::vector<double> m(L + 1, 0.0), pm(L + 2, 0.0), pl(L + 2, 0.0), pn(L + 2, 0.0);
+  pm[0] = 1.0;                 // P_0
+  m[0] += c[0];
+  if (L >= 1) {
+    pl[1] = 1.0;               // P_1
+    m[1] += c[1];
+  }
+  for (int l = 1; l < L; ++l) {
+    std::fill(pn.begin(), pn.end(), 0.0);
+    for (int j = 0; j <= l; ++j) pn[j + 1] += (2.0 * l + 1.0) / (l + 1.0) * pl[j];
+    for (int j = 0; j <= l - 1; ++j) pn[j] -= double(l) / (l + 1.0) * pm[j];
+    for (int j = 0; j <= l + 1; ++j) m[j] += c[l + 1] * pn[j];
+    pm.swap(pl);
+    pl.swap(pn);
+  }
+  auto recentre = [](const std::vector<double>& s) {
+    // sum_j s_j (v + 1/2)^j = sum_k r_k v^k
+    const int n = (int)s.size();
+    std::vector<double> r(n, 0.0);
+    for (int j = 0; j < n; ++j) {
+      double binom = 1.0;   // C(j, k) (1/2)^(j-k), k from j down to 0
+      double pw = 1.0;
+      for (int k = j; k >= 0; --k) {
+        r[k] += s[j] * binom * pw;
+        binom = binom * k / double(j - k + 1);
+        pw *= 0.5;
+      }
+    }
+    return r;
+  };
+  std::vector<double> se, so;
+  for (int j = 0; j <= L; j += 2) se.push_back(m[j]);
+  for (int j = 1; j <= L; j += 2) so.push_back(m[j]);
+  e = recentre(se);
+  o = recentre(so);
 }
 
 bool axis_ok(int n) { return z_supported(n); }
@@ -493,7 +535,21 @@ os3d_status os3d_make_wavelets(const int dims[3], const double* orient, int n_o,
   const std::vector<double> ch = legendre_to_chebyshev(b->c);
   for (int j = 0; j <= kMaxL; ++j) b->h.a[j] = j <= L ? (float)ch[j] : 0.f;
   b->h.c0 = (float)b->c[0];
-  b->lpad = L <= 16 ? 16 : 32;
+  // split monomial form h(t) = E(t^2 - 1/2) + t O(t^2 - 1/2) when it is well conditioned
+  b->ev = 2;
+  if (L <= 24) {
+    std::vector<double> e, o;
+    split_monomial(b->c, e, o);
+    double hmax = 0.0, amp = 0.0;
+    for (int q = 0; q <= 2000; ++q) hmax = std::max(hmax, std::fabs(legendre_sum(b->c, -1.0 + q / 1000.0)));
+    for (double v : e) amp += std::fabs(v);
+    for (double v : o) amp += std::fabs(v);
+    if (hmax > 0.0 && amp <= 4000.0 * hmax) {
+      b->ev = L <= 16 ? 0 : 1;
+      for (int k = 0; k < 13; ++k) b->h.e[k] = k < (int)e.size() ? (float)e[k] : 0.f;
+      for (int k = 0; k < 12; ++k) b->h.o[k] = k < (int)o.size() ? (float)o[k] : 0.f;
+    }
+  }
 
   // (a3) M and the per-voxel factors, FP64
   std::vector<double> sl(4 * nslots);
@@ -631,13 +687,13 @@ os3d_status backward_impl(const os3d_bank* b, const void* U, int udtype, int bat
         for (int d = 0; d < 3; ++d) za.nvec[j][d] = (float)b->orient[3 * ia + d];
       }
       OS3D_CK(counted_launch(OS3D_KIND_XY_INV_SCORE, s, [&] { return launch_xy(ny, nx, XY_INV_SCORE, udtype, xa, nz, ns, s); }));
-      OS3D_CK(counted_launch(OS3D_KIND_Z_INV_SCORE, s, [&] { return launch_z(nz, Z_INV_SCORE, b->lpad, za, ztiles, s); }));
+      OS3D_CK(counted_launch(OS3D_KIND_Z_INV_SCORE, s, [&] { return launch_z(nz, Z_INV_SCORE, b->ev, za, ztiles, s); }));
     }
     ZArgs zf = zargs_base(b);
     zf.in = w.A;
     zf.out = w.T0;
     zf.mult = use_m ? b->GM : b->Gs;
-    OS3D_CK(counted_launch(OS3D_KIND_Z_INV_FINAL, s, [&] { return launch_z(nz, Z_INV_FINAL, b->lpad, zf, ztiles, s); }));
+    OS3D_CK(counted_launch(OS3D_KIND_Z_INV_FINAL, s, [&] { return launch_z(nz, Z_INV_FINAL, b->ev, zf, ztiles, s); }));
     const XYArgs xf = xyargs_one(w.T0, 0, fout, (long long)v * n);
     OS3D_CK(counted_launch(OS3D_KIND_XY_INV_REAL, s, [&] { return launch_xy(ny, nx, XY_INV_REAL, 0, xf, nz, 1, s); }));
   }
@@ -666,7 +722,7 @@ os3d_status os3d_forward(const os3d_bank* b, const float* f, int batch, void* U,
     zp.in = w.T0;
     zp.out = w.fh;
     zp.mult = b->Gs;
-    OS3D_CK(counted_launch(OS3D_KIND_Z_FWD_PREP, s, [&] { return launch_z(nz, Z_FWD_PREP, b->lpad, zp, ztiles, s); }));
+    OS3D_CK(counted_launch(OS3D_KIND_Z_FWD_PREP, s, [&] { return launch_z(nz, Z_FWD_PREP, b->ev, zp, ztiles, s); }));
     // (a5) per block of orientation pairs
     for (int s0 = 0; s0 < nslots; s0 += b->block_slots) {
       const int ns = std::min(b->block_slots, nslots - s0);
@@ -685,7 +741,7 @@ os3d_status os3d_forward(const os3d_bank* b, const float* f, int batch, void* U,
         xa.out_a[j] = ((long long)v * b->n_o + ia) * n;
         xa.out_b[j] = ib >= 0 ? ((long long)v * b->n_o + ib) * n : -1;
       }
-      OS3D_CK(counted_launch(OS3D_KIND_Z_FWD_SCORE, s, [&] { return launch_z(nz, Z_FWD_SCORE, b->lpad, za, ztiles, s); }));
+      OS3D_CK(counted_launch(OS3D_KIND_Z_FWD_SCORE, s, [&] { return launch_z(nz, Z_FWD_SCORE, b->ev, za, ztiles, s); }));
       OS3D_CK(counted_launch(OS3D_KIND_XY_FWD_SCORE, s, [&] { return launch_xy(ny, nx, XY_FWD_SCORE, udtype, xa, nz, ns, s); }));
     }
   }

@@ -10,8 +10,12 @@ constexpr int kMaxSlots = 8;    // orientation slots per launch block
 constexpr int kMaxL = 32;       // maximal Legendre degree
 constexpr int kTileX = 16;      // x-width of a z-pencil tile
 
-// Chebyshev form of the angular profile h(t) = sum_j a_j T_j(t), t in [-1, 1].
+// The angular profile h(t), t = w_hat . n in [-1, 1], in two forms:
+//  e, o: h(t) = E(v) + t O(v), v = t^2 - 1/2, E and O as monomials in v;
+//  a:    h(t) = sum_j a_j T_j(t) (Chebyshev), for when e, o cancel badly.
 struct HEval {
+  float e[13];
+  float o[12];
   float a[kMaxL + 1];
   float c0;   // value used at w = 0: the spherical mean of h
 };
@@ -35,6 +39,8 @@ struct ZArgs {
 struct XYArgs {
   const void* in;
   void* out;
+  int nz;                       // planes per volume
+  int nplanes;                  // nz * slots in this launch
   long long in_a[kMaxSlots];    // element offset of the slot's input volume
   long long in_b[kMaxSlots];    // second input (antipode) or -1
   long long out_a[kMaxSlots];   // element offset of the slot's output volume
@@ -42,7 +48,7 @@ struct XYArgs {
 };
 
 // launchers (return cudaGetLastError of the launch)
-cudaError_t launch_z(int nz, int mode, int lpad, const ZArgs& a, int grid, cudaStream_t s);
+cudaError_t launch_z(int nz, int mode, int ev, const ZArgs& a, int grid, cudaStream_t s);
 cudaError_t launch_xy(int ny, int nx, int mode, int ubf16, const XYArgs& a, int nz, int nslots,
                       cudaStream_t s);
 bool xy_supported(int ny, int nx);
