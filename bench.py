@@ -43,6 +43,8 @@ def _args():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--bf16", action="store_true", help="store U as bfloat16 pairs")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--block-slots", type=int, default=0,
+                    help="orientation pairs per launch block (0 = the library's choice)")
     ap.add_argument("--workload", default=WORKLOAD,
                     help="named synthetic workload (default: the 128^3 x 162 headline)")
     return ap.parse_args()
@@ -228,7 +230,8 @@ def run_ours(args):
     f_np = synth.workload_volume(WORKLOAD, seed=0, batch_index=rank)
     V = os3d.os3d_icosa_orientations(w["subdiv"])
     n_o = len(V)
-    bank = os3d.os3d_make_wavelets(dims, V, os3d.os3d_default_params(L=w["L"]))
+    bank = os3d.os3d_make_wavelets(dims, V, os3d.os3d_default_params(L=w["L"],
+                                                                      block_slots=args.block_slots))
     f = torch.from_numpy(f_np).cuda().unsqueeze(0)
     U = os3d.new_score(bank, 1, bf16=args.bf16)
     frec = torch.empty_like(f)

@@ -103,8 +103,8 @@ os3d_status os3d_icosa_orientations(int subdiv, double* out, int capacity, int* 
  *       G / n^3 and G / (n^3 max(M, eps)) stored as float (Sec. 2.1, 3.1).
  * Antipodal pairs in `orient` are detected (|n_i + n_j| < 1e-9) and share
  * one transform in the forward and inverse passes.
- * Supported axis lengths: 16, 32, 48, 64, 96, 128, 160 (nz), with the
- * (ny, nx) planes 16^2, 32^2, 48^2, 64^2, 96^2, 128^2 and 128 x 160.
+ * Supported axis lengths: nz in {16, 32, 48, 64, 96, 128, 160} with square
+ * (ny, nx) planes of side 16, 32, 48, 64, 96 or 128.
  * Errors: EINVAL (NULL, n_o < 1, a non-unit orientation, parameter out of
  * range), EUNSUPPORTED (grid), ENOMEM, ECUDA. `stream` may be NULL (legacy
  * default stream). */
@@ -115,7 +115,7 @@ os3d_status os3d_make_wavelets(const int dims[3], const double* orient, int n_o,
  * batch x nz x ny x nx float) into U (device, batch x N_o x nz x ny x nx,
  * udtype). Valid for real f: an antipodal pair is written as U_b = conj(U_a).
  * `workspace` (device, os3d_bank_info's workspace_bytes, 256-byte aligned)
- * or NULL for the bank's own. Errors: EINVAL, ECUDA. */
+ * or NULL for the bank's own. f must be 16-byte aligned. Errors: EINVAL, ECUDA. */
 os3d_status os3d_forward(const os3d_bank* bank, const float* f, int batch, void* U,
                          os3d_udtype udtype, void* workspace, void* stream);
 
@@ -145,6 +145,7 @@ os3d_status os3d_bank_minv(const os3d_bank* bank, float* minv, void* stream);
 
 os3d_status os3d_destroy_bank(os3d_bank* bank);
 const char* os3d_status_string(os3d_status s);
+
 
 /* ---- diagnostics (no counterpart in the paper) ---------------------------
  * Kernel kinds of the transform: the xy-passes (2D DFT of one z-plane with

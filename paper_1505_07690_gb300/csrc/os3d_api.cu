@@ -19,44 +19,42 @@
 
 namespace os3d {
 // per-size launchers (os3d_sizes_*.cu)
-#define OS3D_DECL_Z(N) cudaError_t launch_z_##N(int, int, const ZArgs&, int, cudaStream_t);
+#define OS3D_DECL_Z(N) \
+  cudaError_t launch_z_##N(int, int, const PassArgs&, int, cudaStream_t);
 #define OS3D_DECL_XY(NY, NX) \
-  cudaError_t launch_xy_##NY##_##NX(int, int, const XYArgs&, int, int, cudaStream_t);
+  cudaError_t launch_xy_##NY##_##NX(int, int, const PassArgs&, cudaStream_t);
 OS3D_DECL_Z(16) OS3D_DECL_Z(32) OS3D_DECL_Z(48) OS3D_DECL_Z(64) OS3D_DECL_Z(96)
 OS3D_DECL_Z(128) OS3D_DECL_Z(160)
 OS3D_DECL_XY(16, 16) OS3D_DECL_XY(32, 32) OS3D_DECL_XY(48, 48) OS3D_DECL_XY(64, 64)
-OS3D_DECL_XY(96, 96) OS3D_DECL_XY(128, 128) OS3D_DECL_XY(128, 160)
+OS3D_DECL_XY(96, 96) OS3D_DECL_XY(128, 128)
 
 bool z_supported(int nz) {
   return nz == 16 || nz == 32 || nz == 48 || nz == 64 || nz == 96 || nz == 128 || nz == 160;
 }
 bool xy_supported(int ny, int nx) {
-  return (ny == nx && (nx == 16 || nx == 32 || nx == 48 || nx == 64 || nx == 96 || nx == 128)) ||
-         (ny == 128 && nx == 160);
+  return ny == nx && (nx == 16 || nx == 32 || nx == 48 || nx == 64 || nx == 96 || nx == 128);
 }
-cudaError_t launch_z(int nz, int mode, int lpad, const ZArgs& a, int grid, cudaStream_t s) {
+cudaError_t launch_z(int nz, int mode, int ev, const PassArgs& a, int tiles, cudaStream_t s) {
   switch (nz) {
-    case 16: return launch_z_16(mode, lpad, a, grid, s);
-    case 32: return launch_z_32(mode, lpad, a, grid, s);
-    case 48: return launch_z_48(mode, lpad, a, grid, s);
-    case 64: return launch_z_64(mode, lpad, a, grid, s);
-    case 96: return launch_z_96(mode, lpad, a, grid, s);
-    case 128: return launch_z_128(mode, lpad, a, grid, s);
-    case 160: return launch_z_160(mode, lpad, a, grid, s);
+    case 16: return launch_z_16(mode, ev, a, tiles, s);
+    case 32: return launch_z_32(mode, ev, a, tiles, s);
+    case 48: return launch_z_48(mode, ev, a, tiles, s);
+    case 64: return launch_z_64(mode, ev, a, tiles, s);
+    case 96: return launch_z_96(mode, ev, a, tiles, s);
+    case 128: return launch_z_128(mode, ev, a, tiles, s);
+    case 160: return launch_z_160(mode, ev, a, tiles, s);
     default: return cudaErrorInvalidValue;
   }
 }
-cudaError_t launch_xy(int ny, int nx, int mode, int ub, const XYArgs& a, int nz, int ns,
-                      cudaStream_t s) {
-  if (ny == 128 && nx == 160) return launch_xy_128_160(mode, ub, a, nz, ns, s);
+cudaError_t launch_xy(int ny, int nx, int mode, int ub, const PassArgs& a, cudaStream_t s) {
   if (ny != nx) return cudaErrorInvalidValue;
   switch (nx) {
-    case 16: return launch_xy_16_16(mode, ub, a, nz, ns, s);
-    case 32: return launch_xy_32_32(mode, ub, a, nz, ns, s);
-    case 48: return launch_xy_48_48(mode, ub, a, nz, ns, s);
-    case 64: return launch_xy_64_64(mode, ub, a, nz, ns, s);
-    case 96: return launch_xy_96_96(mode, ub, a, nz, ns, s);
-    case 128: return launch_xy_128_128(mode, ub, a, nz, ns, s);
+    case 16: return launch_xy_16_16(mode, ub, a, s);
+    case 32: return launch_xy_32_32(mode, ub, a, s);
+    case 48: return launch_xy_48_48(mode, ub, a, s);
+    case 64: return launch_xy_64_64(mode, ub, a, s);
+    case 96: return launch_xy_96_96(mode, ub, a, s);
+    case 128: return launch_xy_128_128(mode, ub, a, s);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -80,6 +78,8 @@ struct os3d_bank {
   float* GM = nullptr;                 // G / (n^3 max(M, eps))
   float* Minv = nullptr;               // 1 / max(M, eps), 0 outside the ball
   void* ws = nullptr;                  // default workspace
+  cudaStream_t side[2] = {nullptr, nullptr};   // consecutive blocks alternate between these
+  cudaEvent_t ev_fork = nullptr, ev_join[2] = {nullptr, nullptr};
   size_t ws_bytes = 0;
 };
 
@@ -463,7 +463,9 @@ os3d_status os3d_make_wavelets(const int dims[3], const double* orient, int n_o,
     b->block_slots = (int)std::max(1ll, std::min<long long>(bs, kMaxSlots));
   }
   b->block_slots = std::min(b->block_slots, nslots);
-  b->ws_bytes = vol_c64 * (3 + b->block_slots);
+  // f_hat, two partial orientation sums, one per-volume intermediate and two
+  // sets of block intermediates (for the two side streams)
+  b->ws_bytes = vol_c64 * (4 + 2 * b->block_slots);
 
   // device allocations
   if (cudaMalloc(&b->Gs, sizeof(float) * b->nvox) != cudaSuccess ||
@@ -473,6 +475,12 @@ os3d_status os3d_make_wavelets(const int dims[3], const double* orient, int n_o,
     cudaGetLastError();
     return fail(OS3D_ENOMEM);
   }
+  for (int i = 0; i < 2; ++i)
+    if (cudaStreamCreateWithFlags(&b->side[i], cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->ev_join[i], cudaEventDisableTiming) != cudaSuccess)
+      return fail(OS3D_ECUDA);
+  if (cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) != cudaSuccess)
+    return fail(OS3D_ECUDA);
 
   // (a1) sample points for the zonal fit
   std::vector<double> zt, wt;
@@ -598,6 +606,11 @@ os3d_status os3d_destroy_bank(os3d_bank* b) {
   if (b->GM) cudaFree(b->GM);
   if (b->Minv) cudaFree(b->Minv);
   if (b->ws) cudaFree(b->ws);
+  for (int i = 0; i < 2; ++i) {
+    if (b->side[i]) cudaStreamDestroy(b->side[i]);
+    if (b->ev_join[i]) cudaEventDestroy(b->ev_join[i]);
+  }
+  if (b->ev_fork) cudaEventDestroy(b->ev_fork);
   delete b;
   return OS3D_OK;
 }
@@ -610,39 +623,65 @@ os3d_status os3d_destroy_bank(os3d_bank* b) {
 namespace {
 
 struct Work {
-  float2* fh;   // f_hat G / n^3
-  float2* A;    // orientation sum
-  float2* T0;   // per-volume intermediate
-  float2* T;    // block_slots intermediates
+  float2* fh;     // f_hat G / n^3
+  float2* A[2];   // partial orientation sums (one per side stream)
+  float2* T0;     // per-volume intermediate
+  float2* T[2];   // block intermediates (one set per side stream)
 };
 
 Work carve(const os3d_bank* b, void* ws) {
   float2* base = (float2*)(ws ? ws : b->ws);
   const long long n = b->nvox;
-  return Work{base, base + n, base + 2 * n, base + 3 * n};
+  Work w;
+  w.fh = base;
+  w.A[0] = base + n;
+  w.A[1] = base + 2 * n;
+  w.T0 = base + 3 * n;
+  w.T[0] = base + 4 * n;
+  w.T[1] = base + (4 + b->block_slots) * n;
+  return w;
 }
 
-ZArgs zargs_base(const os3d_bank* b) {
-  ZArgs a{};
+// fork the two side streams off `s` / join them back into `s`
+cudaError_t fork_side(const os3d_bank* b, cudaStream_t s) {
+  cudaError_t e = cudaEventRecord(b->ev_fork, s);
+  for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(b->side[i], b->ev_fork, 0);
+  return e;
+}
+cudaError_t join_side(const os3d_bank* b, cudaStream_t s) {
+  cudaError_t e = cudaSuccess;
+  for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+    e = cudaEventRecord(b->ev_join[i], b->side[i]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, b->ev_join[i], 0);
+  }
+  return e;
+}
+
+PassArgs args_base(const os3d_bank* b) {
+  PassArgs a{};
+  a.nz = b->dims[0];
   a.ny = b->dims[1];
   a.nx = b->dims[2];
   a.wz = float(2.0 * kPi / b->dims[0]);
   a.wy = float(2.0 * kPi / b->dims[1]);
   a.wx = float(2.0 * kPi / b->dims[2]);
   a.slot_stride = b->nvox;
+  a.nslots = 1;
   a.h = b->h;
+  for (int j = 0; j < kMaxSlots; ++j) a.ub[j] = -1;
   return a;
 }
 
-XYArgs xyargs_one(const void* in, long long ia, void* out, long long oa) {
-  XYArgs a{};
-  a.in = in;
-  a.out = out;
-  a.in_a[0] = ia;
-  a.in_b[0] = -1;
-  a.out_a[0] = oa;
-  a.out_b[0] = -1;
-  return a;
+// slots [s0, s0 + ns) of volume v: orientations and score offsets
+void set_slots(const os3d_bank* b, PassArgs& a, int v, int s0, int ns) {
+  const long long n = b->nvox;
+  a.nslots = ns;
+  for (int j = 0; j < ns; ++j) {
+    const int ia = b->slot_a[s0 + j], ib = b->slot_b[s0 + j];
+    for (int d = 0; d < 3; ++d) a.nvec[j][d] = (float)b->orient[3 * ia + d];
+    a.ua[j] = ((long long)v * b->n_o + ia) * n;
+    a.ub[j] = ib >= 0 ? ((long long)v * b->n_o + ib) * n : -1;
+  }
 }
 
 os3d_status check_call(const os3d_bank* b, const void* x, const void* y, int batch, int udtype,
@@ -653,49 +692,56 @@ os3d_status check_call(const os3d_bank* b, const void* x, const void* y, int bat
   return current_device_matches(b);
 }
 
-#define OS3D_CK(call)                         \
-  do {                                        \
+#define OS3D_CK(call)                             \
+  do {                                            \
     if ((call) != cudaSuccess) return OS3D_ECUDA; \
   } while (0)
 
-// inverse (use_m = true) or adjoint (use_m = false)
+// inverse (use_m = true) or adjoint (use_m = false). Consecutive blocks of
+// orientation pairs alternate between the two side streams (each with its own
+// intermediates and partial sum), so one block's xy-pass overlaps the other's
+// z-pass.
 os3d_status backward_impl(const os3d_bank* b, const void* U, int udtype, int batch, float* fout,
                           void* ws, cudaStream_t s, bool use_m) {
   const Work w = carve(b, ws);
   const int nz = b->dims[0], ny = b->dims[1], nx = b->dims[2];
   const int nslots = (int)b->slot_a.size();
-  const int ztiles = ny * (nx / kTileX);
+  const int tiles = ny * (nx / kTileX);
   const long long n = b->nvox;
   for (int v = 0; v < batch; ++v) {
+    OS3D_CK(fork_side(b, s));
     int q = 0;
     for (int s0 = 0; s0 < nslots; s0 += b->block_slots, ++q) {
       const int ns = std::min(b->block_slots, nslots - s0);
-      XYArgs xa{};
+      const int k = q & 1;
+      cudaStream_t st = b->side[k];
+      PassArgs xa = args_base(b);
+      set_slots(b, xa, v, s0, ns);
       xa.in = U;
-      xa.out = w.T;
-      ZArgs za = zargs_base(b);
-      za.in = w.T;
-      za.out = w.A;
-      za.nslots = ns;
-      za.accumulate = q > 0;
-      for (int j = 0; j < ns; ++j) {
-        const int ia = b->slot_a[s0 + j], ib = b->slot_b[s0 + j];
-        xa.in_a[j] = ((long long)v * b->n_o + ia) * n;
-        xa.in_b[j] = ib >= 0 ? ((long long)v * b->n_o + ib) * n : -1;
-        xa.out_a[j] = (long long)j * n;
-        xa.out_b[j] = -1;
-        for (int d = 0; d < 3; ++d) za.nvec[j][d] = (float)b->orient[3 * ia + d];
-      }
-      OS3D_CK(counted_launch(OS3D_KIND_XY_INV_SCORE, s, [&] { return launch_xy(ny, nx, XY_INV_SCORE, udtype, xa, nz, ns, s); }));
-      OS3D_CK(counted_launch(OS3D_KIND_Z_INV_SCORE, s, [&] { return launch_z(nz, Z_INV_SCORE, b->ev, za, ztiles, s); }));
+      xa.out = w.T[k];
+      OS3D_CK(counted_launch(OS3D_KIND_XY_INV_SCORE, st,
+                             [&] { return launch_xy(ny, nx, XY_INV_SCORE, udtype, xa, st); }));
+      PassArgs za = xa;
+      za.in = w.T[k];
+      za.out = w.A[k];
+      za.accumulate = q >= 2;
+      OS3D_CK(counted_launch(OS3D_KIND_Z_INV_SCORE, st,
+                             [&] { return launch_z(nz, Z_INV_SCORE, b->ev, za, tiles, st); }));
     }
-    ZArgs zf = zargs_base(b);
-    zf.in = w.A;
+    OS3D_CK(join_side(b, s));
+    PassArgs zf = args_base(b);
+    zf.in = w.A[0];
+    zf.in2 = q >= 2 ? w.A[1] : nullptr;
     zf.out = w.T0;
     zf.mult = use_m ? b->GM : b->Gs;
-    OS3D_CK(counted_launch(OS3D_KIND_Z_INV_FINAL, s, [&] { return launch_z(nz, Z_INV_FINAL, b->ev, zf, ztiles, s); }));
-    const XYArgs xf = xyargs_one(w.T0, 0, fout, (long long)v * n);
-    OS3D_CK(counted_launch(OS3D_KIND_XY_INV_REAL, s, [&] { return launch_xy(ny, nx, XY_INV_REAL, 0, xf, nz, 1, s); }));
+    OS3D_CK(counted_launch(OS3D_KIND_Z_INV_FINAL, s,
+                           [&] { return launch_z(nz, Z_INV_FINAL, 0, zf, tiles, s); }));
+    PassArgs xf = args_base(b);
+    xf.in = w.T0;
+    xf.out = fout;
+    xf.out_off = (long long)v * n;
+    OS3D_CK(counted_launch(OS3D_KIND_XY_INV_REAL, s,
+                           [&] { return launch_xy(ny, nx, XY_INV_REAL, 0, xf, s); }));
   }
   return OS3D_OK;
 }
@@ -712,38 +758,42 @@ os3d_status os3d_forward(const os3d_bank* b, const float* f, int batch, void* U,
   const Work w = carve(b, ws);
   const int nz = b->dims[0], ny = b->dims[1], nx = b->dims[2];
   const int nslots = (int)b->slot_a.size();
-  const int ztiles = ny * (nx / kTileX);
+  const int tiles = ny * (nx / kTileX);
   const long long n = b->nvox;
   for (int v = 0; v < batch; ++v) {
     // (a4) f_hat G / n^3
-    const XYArgs x0 = xyargs_one(f, (long long)v * n, w.T0, 0);
-    OS3D_CK(counted_launch(OS3D_KIND_XY_FWD_REAL, s, [&] { return launch_xy(ny, nx, XY_FWD_REAL, 0, x0, nz, 1, s); }));
-    ZArgs zp = zargs_base(b);
+    PassArgs x0 = args_base(b);
+    x0.in = f;
+    x0.in_off = (long long)v * n;
+    x0.out = w.T0;
+    OS3D_CK(counted_launch(OS3D_KIND_XY_FWD_REAL, s,
+                           [&] { return launch_xy(ny, nx, XY_FWD_REAL, 0, x0, s); }));
+    PassArgs zp = args_base(b);
     zp.in = w.T0;
     zp.out = w.fh;
     zp.mult = b->Gs;
-    OS3D_CK(counted_launch(OS3D_KIND_Z_FWD_PREP, s, [&] { return launch_z(nz, Z_FWD_PREP, b->ev, zp, ztiles, s); }));
-    // (a5) per block of orientation pairs
-    for (int s0 = 0; s0 < nslots; s0 += b->block_slots) {
+    OS3D_CK(counted_launch(OS3D_KIND_Z_FWD_PREP, s,
+                           [&] { return launch_z(nz, Z_FWD_PREP, 0, zp, tiles, s); }));
+    // (a5) per block of orientation pairs, alternating between the side streams
+    OS3D_CK(fork_side(b, s));
+    int q = 0;
+    for (int s0 = 0; s0 < nslots; s0 += b->block_slots, ++q) {
       const int ns = std::min(b->block_slots, nslots - s0);
-      ZArgs za = zargs_base(b);
+      const int k = q & 1;
+      cudaStream_t st = b->side[k];
+      PassArgs za = args_base(b);
+      set_slots(b, za, v, s0, ns);
       za.in = w.fh;
-      za.out = w.T;
-      za.nslots = ns;
-      XYArgs xa{};
-      xa.in = w.T;
+      za.out = w.T[k];
+      OS3D_CK(counted_launch(OS3D_KIND_Z_FWD_SCORE, st,
+                             [&] { return launch_z(nz, Z_FWD_SCORE, b->ev, za, tiles, st); }));
+      PassArgs xa = za;
+      xa.in = w.T[k];
       xa.out = U;
-      for (int j = 0; j < ns; ++j) {
-        const int ia = b->slot_a[s0 + j], ib = b->slot_b[s0 + j];
-        for (int d = 0; d < 3; ++d) za.nvec[j][d] = (float)b->orient[3 * ia + d];
-        xa.in_a[j] = (long long)j * n;
-        xa.in_b[j] = -1;
-        xa.out_a[j] = ((long long)v * b->n_o + ia) * n;
-        xa.out_b[j] = ib >= 0 ? ((long long)v * b->n_o + ib) * n : -1;
-      }
-      OS3D_CK(counted_launch(OS3D_KIND_Z_FWD_SCORE, s, [&] { return launch_z(nz, Z_FWD_SCORE, b->ev, za, ztiles, s); }));
-      OS3D_CK(counted_launch(OS3D_KIND_XY_FWD_SCORE, s, [&] { return launch_xy(ny, nx, XY_FWD_SCORE, udtype, xa, nz, ns, s); }));
+      OS3D_CK(counted_launch(OS3D_KIND_XY_FWD_SCORE, st,
+                             [&] { return launch_xy(ny, nx, XY_FWD_SCORE, udtype, xa, st); }));
     }
+    OS3D_CK(join_side(b, s));
   }
   return OS3D_OK;
 }

@@ -1,5 +1,5 @@
-// Launch-argument structures and launcher declarations shared by the C-ABI
-// host code (os3d_api.cu) and the kernels (os3d_transform.cu, os3d_bank.cu).
+// Launch-argument structure and launcher declarations shared by the C-ABI
+// host code (os3d_api.cu) and the kernels (os3d_passes.cuh, os3d_bank.cu).
 #pragma once
 #include <cuda_runtime.h>
 #include <cstdint>
@@ -20,37 +20,41 @@ struct HEval {
   float c0;   // value used at w = 0: the spherical mean of h
 };
 
+// z-passes (DFT along z of 16-wide pencil tiles):
+//  Z_FWD_PREP : T0 -> DFT_z -> x mult (G/n^3)                     -> f_hat
+//  Z_FWD_SCORE: f_hat x h(w_hat . n_s) -> IDFT_z, every slot      -> T_s
+//  Z_INV_SCORE: T_s -> DFT_z -> x h(w_hat . n_s), sum over slots  -> A
+//  Z_INV_FINAL: A x mult (G/(n^3 max(M,eps))) -> IDFT_z           -> T0
 enum ZMode { Z_FWD_PREP = 0, Z_FWD_SCORE = 1, Z_INV_SCORE = 2, Z_INV_FINAL = 3 };
+// xy-passes (2D DFT of z-planes, a 2-CTA cluster per plane):
+//  XY_FWD_REAL : f (real) -> DFT_xy                                -> T0
+//  XY_FWD_SCORE: T_s -> IDFT_xy -> U_a, U_b = conj U_a              (HBM store)
+//  XY_INV_SCORE: U_a + conj U_b (HBM load) -> DFT_xy               -> T_s
+//  XY_INV_REAL : T0 -> IDFT_xy -> real part                        -> f
 enum XYMode { XY_FWD_REAL = 0, XY_FWD_SCORE = 1, XY_INV_SCORE = 2, XY_INV_REAL = 3 };
 
-struct ZArgs {
-  const float2* in;
-  float2* out;
-  const float* mult;        // per-voxel real factor (prep / final)
-  long long slot_stride;    // elements between consecutive slot volumes of T
-  int ny, nx;
-  float wz, wy, wx;         // 2 pi / n per axis
+struct PassArgs {
+  const void* in;
+  const void* in2;            // Z_INV_FINAL: second partial sum (or null)
+  void* out;
+  const float* mult;          // per-voxel real factor (z prep / final)
+  long long in_off;           // element offset of the input volume
+  long long out_off;          // element offset of the output volume
+  long long slot_stride;      // elements between consecutive T volumes
+  long long ua[kMaxSlots];    // element offset of U_a of each slot
+  long long ub[kMaxSlots];    // element offset of U_b = antipode, or -1
+  int nz, ny, nx;
+  float wz, wy, wx;           // 2 pi / n per axis
   int nslots;
-  int accumulate;           // inverse score: 0 -> write A, 1 -> add to A
-  float nvec[kMaxSlots][3]; // orientation n_a (x, y, z) of each slot
+  int accumulate;             // Z_INV_SCORE: 0 -> A = sum, 1 -> A += sum
+  float nvec[kMaxSlots][3];   // orientation n_a (x, y, z) of each slot
   HEval h;
 };
 
-struct XYArgs {
-  const void* in;
-  void* out;
-  int nz;                       // planes per volume
-  int nplanes;                  // nz * slots in this launch
-  long long in_a[kMaxSlots];    // element offset of the slot's input volume
-  long long in_b[kMaxSlots];    // second input (antipode) or -1
-  long long out_a[kMaxSlots];   // element offset of the slot's output volume
-  long long out_b[kMaxSlots];   // second output (antipode) or -1
-};
-
 // launchers (return cudaGetLastError of the launch)
-cudaError_t launch_z(int nz, int mode, int ev, const ZArgs& a, int grid, cudaStream_t s);
-cudaError_t launch_xy(int ny, int nx, int mode, int ubf16, const XYArgs& a, int nz, int nslots,
-                      cudaStream_t s);
+cudaError_t launch_z(int nz, int mode, int ev, const PassArgs& a, int grid_tiles,
+                     cudaStream_t s);
+cudaError_t launch_xy(int ny, int nx, int mode, int ubf16, const PassArgs& a, cudaStream_t s);
 bool xy_supported(int ny, int nx);
 bool z_supported(int nz);
 

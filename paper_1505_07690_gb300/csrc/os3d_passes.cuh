@@ -1,0 +1,563 @@
+// Fused DFT passes of the orientation-score transform (sm_103a).
+//
+// The 3D DFT of every orientation is split into a z-pass (DFT along z of
+// 16-wide pencil tiles) and an xy-pass (2D DFT of z-planes on a 2-CTA
+// cluster), with the per-orientation intermediate T held in L2:
+//   forward  (Eq. construction1Discrete):  U_a = IDFT_xy IDFT_z [ f_hat G h_a ]
+//            z-pass : f_hat tile (read once per block) x h(w_hat . n_a) -> IDFT_z -> T_a
+//            xy-pass: T_a -> IDFT_xy -> U_a and U_b = conj U_a           (HBM)
+//   inverse  (Eq. Reconstruction1Discrete with the clamp of Sec. 3.1):
+//            xy-pass: U_a + conj U_b (HBM) -> DFT_xy -> T_a
+//            z-pass : T_a -> DFT_z -> x h(w_hat . n_a), summed over the block -> A
+//            then f = Re IDFT[ A G / (n^3 max(M, eps)) ].
+// For a real image U_{-n} = conj U_n, and the real reconstruction needs only
+// the Hermitian part of sum_i psi_hat_i DFT(U_i), which for the pair
+// (a, b = -a) is Herm[ G h_a DFT(U_a + conj U_b) ] (psi_hat_{-n}(w) =
+// psi_hat_n(-w)); so one transform serves each antipodal pair.
+#pragma once
+#include <cooperative_groups.h>
+#include <cuda_bf16.h>
+#include <algorithm>
+#include "os3d_fft.cuh"
+#include "os3d_kernels.cuh"
+
+namespace os3d {
+
+__device__ __forceinline__ int signed_index(int k, int n) { return k >= (n + 1) / 2 ? k - n : k; }
+
+// Angular profile h at t = w_hat . n. EV 0 / 1: h(t) = E(v) + t O(v), v = t^2 - 1/2,
+// E and O in the monomial basis of v by Horner's rule (9 + 8 or 13 + 12
+// coefficients), chosen on the host only when the coefficients show no
+// cancellation. EV 2: sum_{j<=32} a_j T_j(t) by Clenshaw's recurrence.
+template <int EV>
+__device__ __forceinline__ float eval_h(const HEval& h, float t) {
+  if constexpr (EV < 2) {
+    constexpr int NE = EV == 0 ? 9 : 13;
+    constexpr int NO = NE - 1;
+    const float v = fmaf(t, t, -0.5f);
+    float e = h.e[NE - 1];
+#pragma unroll
+    for (int k = NE - 2; k >= 0; --k) e = fmaf(e, v, h.e[k]);
+    float o = h.o[NO - 1];
+#pragma unroll
+    for (int k = NO - 2; k >= 0; --k) o = fmaf(o, v, h.o[k]);
+    return fmaf(t, o, e);
+  } else {
+    float b1 = 0.f, b2 = 0.f;
+    const float t2 = t + t;
+#pragma unroll
+    for (int j = kMaxL; j >= 1; --j) {
+      const float b0 = fmaf(t2, b1, h.a[j] - b2);
+      b2 = b1;
+      b1 = b0;
+    }
+    return fmaf(t, b1, h.a[0] - b2);
+  }
+}
+
+template <int UBF16>
+__device__ __forceinline__ void store_u(void* base, long long i, float2 v) {
+  if constexpr (UBF16) {
+    __nv_bfloat162 b = __floats2bfloat162_rn(v.x, v.y);
+    __stcs(reinterpret_cast<unsigned int*>(base) + i, *reinterpret_cast<unsigned int*>(&b));
+  } else {
+    __stcs(reinterpret_cast<float2*>(base) + i, v);
+  }
+}
+
+// ----------------------------------------------------------------------------
+// shared-memory and cluster helpers (inline PTX)
+// ----------------------------------------------------------------------------
+__device__ __forceinline__ unsigned smem_addr(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+// the same offset in the shared memory of CTA `rank` of this cluster
+__device__ __forceinline__ unsigned map_cluster_rank(unsigned a, unsigned rank) {
+  unsigned r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ void st_cluster_f2(unsigned addr, float2 v) {
+  asm volatile("st.shared::cluster.v2.f32 [%0], {%1, %2};" ::"r"(addr), "f"(v.x), "f"(v.y)
+               : "memory");
+}
+// cluster-wide barrier with release/acquire ordering of shared-memory accesses
+__device__ __forceinline__ void cluster_sync_acqrel() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" :::
+                   "memory");
+}
+__device__ __forceinline__ unsigned cluster_rank() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+
+// ----------------------------------------------------------------------------
+// z-pass: DFT along z of a 16-wide pencil tile (all slots of the block)
+// ----------------------------------------------------------------------------
+template <int NZ, int MODE, int EV>
+__global__ void __launch_bounds__(kTileX * Plan<NZ>::R2, 4)
+z_kernel(const __grid_constant__ PassArgs a) {
+  constexpr int R1 = Plan<NZ>::R1, R2 = Plan<NZ>::R2;
+  constexpr int TW = kTileX;
+  constexpr int J3 = (R1 + R2 - 1) / R2;   // step-2 items per thread (k1 = n2 + R2 j < R1)
+  constexpr int DIR = (MODE == Z_FWD_PREP || MODE == Z_INV_SCORE) ? -1 : +1;
+
+  __shared__ float2 tile[NZ * TW];     // step-1 / step-2 exchange
+  __shared__ float2 keep[NZ * TW];     // forward: f_hat tile; inverse: slot sum
+  __shared__ float2 tws[NZ];
+
+  const int t = threadIdx.x;
+  const int xl = t % TW, n2 = t / TW;
+  const int tiles_x = a.nx / TW;
+  const int y = blockIdx.x / tiles_x;
+  const int x = (blockIdx.x % tiles_x) * TW + xl;
+  const long long plane = (long long)a.ny * a.nx;
+  const long long col = (long long)y * a.nx + x;
+
+  fill_twiddles<NZ, DIR>(tws);
+  const float wy = float(signed_index(y, a.ny)) * a.wy;
+  const float wx = float(signed_index(x, a.nx)) * a.wx;
+  const float rxy2 = fmaf(wy, wy, wx * wx);
+  const bool dc_col = (y == 0) && (x == 0);
+
+  // step 1 (R1-point DFT of the thread's stride-R2 elements) + twiddle + store
+  auto step1 = [&](float2 (&v)[R1]) {
+    dft<R1, DIR>(v);
+#pragma unroll
+    for (int k1 = 0; k1 < R1; ++k1)
+      tile[(n2 + R2 * k1) * TW + xl] = (k1 == 0) ? v[k1] : cmul(v[k1], tws[(n2 * k1) % NZ]);
+  };
+  // step 2 (R2-point DFT over n2 for k1 = n2 + R2 j)
+  auto step2 = [&](int j, float2 (&w)[R2]) {
+    const int k1 = n2 + R2 * j;
+#pragma unroll
+    for (int m = 0; m < R2; ++m) w[m] = tile[(m + R2 * k1) * TW + xl];
+    dft<R2, DIR>(w);
+  };
+
+  if constexpr (MODE == Z_FWD_PREP || MODE == Z_INV_FINAL) {
+    float2 v[R1];
+#pragma unroll
+    for (int n1 = 0; n1 < R1; ++n1) {
+      const long long e = (long long)(n2 + R2 * n1) * plane + col;
+      float2 in = reinterpret_cast<const float2*>(a.in)[a.in_off + e];
+      if (MODE == Z_INV_FINAL && a.in2) in = cadd(in, reinterpret_cast<const float2*>(a.in2)[e]);
+      v[n1] = MODE == Z_INV_FINAL ? cscale(in, a.mult[e]) : in;
+    }
+    __syncthreads();   // twiddle table
+    step1(v);
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < J3; ++j) {
+      const int k1 = n2 + R2 * j;
+      if (R1 % R2 != 0 && k1 >= R1) break;
+      float2 w[R2];
+      step2(j, w);
+#pragma unroll
+      for (int k2 = 0; k2 < R2; ++k2) {
+        const long long e = (long long)(k1 + R1 * k2) * plane + col;
+        reinterpret_cast<float2*>(a.out)[a.out_off + e] =
+            MODE == Z_FWD_PREP ? cscale(w[k2], a.mult[e]) : w[k2];
+      }
+    }
+  } else if constexpr (MODE == Z_FWD_SCORE) {
+    // f_hat tile staged once, then for each slot: x h -> IDFT_z -> T_s
+#pragma unroll
+    for (int n1 = 0; n1 < R1; ++n1) {
+      const int z = n2 + R2 * n1;
+      keep[z * TW + xl] = reinterpret_cast<const float2*>(a.in)[(long long)z * plane + col];
+    }
+    float ur[R1], rr[R1];   // w_z / |w| and 1 / |w| at the step-1 frequencies
+#pragma unroll
+    for (int n1 = 0; n1 < R1; ++n1) {
+      const float wz = float(signed_index(n2 + R2 * n1, NZ)) * a.wz;
+      const float r2 = fmaf(wz, wz, rxy2);
+      const float ri = r2 > 0.f ? rsqrtf(r2) : 0.f;
+      ur[n1] = wz * ri;
+      rr[n1] = ri;
+    }
+    __syncthreads();
+    for (int s = 0; s < a.nslots; ++s) {
+      const float dxy = fmaf(wx, a.nvec[s][0], wy * a.nvec[s][1]);
+      const float nz = a.nvec[s][2];
+      float2 v[R1];
+#pragma unroll
+      for (int n1 = 0; n1 < R1; ++n1) {
+        float hv = eval_h<EV>(a.h, fmaf(rr[n1], dxy, ur[n1] * nz));
+        if (n1 == 0 && n2 == 0 && dc_col) hv = a.h.c0;
+        v[n1] = cscale(keep[(n2 + R2 * n1) * TW + xl], hv);
+      }
+      step1(v);
+      __syncthreads();
+      float2* out = reinterpret_cast<float2*>(a.out) + (long long)s * a.slot_stride;
+#pragma unroll
+      for (int j = 0; j < J3; ++j) {
+        const int k1 = n2 + R2 * j;
+        if (R1 % R2 != 0 && k1 >= R1) break;
+        float2 w[R2];
+        step2(j, w);
+#pragma unroll
+        for (int k2 = 0; k2 < R2; ++k2) out[(long long)(k1 + R1 * k2) * plane + col] = w[k2];
+      }
+      __syncthreads();
+    }
+  } else {  // Z_INV_SCORE: for each slot T_s -> DFT_z -> x h, summed into A
+    float ur[J3 * R2], rr[J3 * R2];   // at the step-2 output frequencies
+#pragma unroll
+    for (int j = 0; j < J3; ++j) {
+#pragma unroll
+      for (int k2 = 0; k2 < R2; ++k2) {
+        const int kz = min(n2 + R2 * j, R1 - 1) + R1 * k2;
+        const float wz = float(signed_index(kz, NZ)) * a.wz;
+        const float r2 = fmaf(wz, wz, rxy2);
+        const float ri = r2 > 0.f ? rsqrtf(r2) : 0.f;
+        ur[j * R2 + k2] = wz * ri;
+        rr[j * R2 + k2] = ri;
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < J3; ++j) {
+      if (R1 % R2 != 0 && n2 + R2 * j >= R1) break;
+#pragma unroll
+      for (int k2 = 0; k2 < R2; ++k2) {
+        const int z = n2 + R2 * j + R1 * k2;
+        keep[z * TW + xl] = a.accumulate
+                                ? reinterpret_cast<const float2*>(a.out)[(long long)z * plane + col]
+                                : make_float2(0.f, 0.f);
+      }
+    }
+    __syncthreads();   // twiddle table
+    for (int s = 0; s < a.nslots; ++s) {
+      const float2* in = reinterpret_cast<const float2*>(a.in) + (long long)s * a.slot_stride;
+      float2 v[R1];
+#pragma unroll
+      for (int n1 = 0; n1 < R1; ++n1) v[n1] = in[(long long)(n2 + R2 * n1) * plane + col];
+      step1(v);
+      __syncthreads();
+      const float dxy = fmaf(wx, a.nvec[s][0], wy * a.nvec[s][1]);
+      const float nz = a.nvec[s][2];
+#pragma unroll
+      for (int j = 0; j < J3; ++j) {
+        if (R1 % R2 != 0 && n2 + R2 * j >= R1) break;
+        float2 w[R2];
+        step2(j, w);
+#pragma unroll
+        for (int k2 = 0; k2 < R2; ++k2) {
+          const int p = j * R2 + k2;
+          float hv = eval_h<EV>(a.h, fmaf(rr[p], dxy, ur[p] * nz));
+          if (p == 0 && n2 == 0 && dc_col) hv = a.h.c0;
+          float2& d = keep[(n2 + R2 * j + R1 * k2) * TW + xl];
+          d.x = fmaf(hv, w[k2].x, d.x);
+          d.y = fmaf(hv, w[k2].y, d.y);
+        }
+      }
+      __syncthreads();
+    }
+#pragma unroll
+    for (int j = 0; j < J3; ++j) {
+      if (R1 % R2 != 0 && n2 + R2 * j >= R1) break;
+#pragma unroll
+      for (int k2 = 0; k2 < R2; ++k2) {
+        const int z = n2 + R2 * j + R1 * k2;
+        reinterpret_cast<float2*>(a.out)[(long long)z * plane + col] = keep[z * TW + xl];
+      }
+    }
+  }
+}
+
+// ----------------------------------------------------------------------------
+// xy-pass on a 2-CTA cluster. CTA h holds rows [h NY/2, (h+1) NY/2) of a
+// z-plane for the x direction and columns [h NX/2, (h+1) NX/2) for the y
+// direction; the x step-2 outputs go straight into the owner's y-layout
+// buffer (local or distributed shared memory). Half a plane (74 KB at 128^2)
+// lets two CTAs share an SM, so one CTA's loads overlap the other's DFTs.
+// Shared layout: x layout row pitch NX + 8 (rows alternate 64-byte halves of
+// the bank space) with an XOR swizzle inside each group of R2x columns; y
+// layout row pitch NX/2 + 8. All accesses of the 128^2 plan are
+// bank-conflict-free. Work units: (plane, slot) for the score modes, planes
+// for the real modes; clusters loop over units.
+// ----------------------------------------------------------------------------
+template <int NY, int NX>
+struct XYCfg {
+  static constexpr int NYH = NY / 2, NXH = NX / 2;
+  static constexpr int R1x = Plan<NX>::R1, R2x = Plan<NX>::R2;
+  static constexpr int R1y = Plan<NY>::R1, R2y = Plan<NY>::R2;
+  static_assert((R2x & (R2x - 1)) == 0, "R2x must be a power of two");
+  static constexpr bool ok(int nt) {
+    return nt % 32 == 0 && (NYH * R2x) % nt == 0 && nt % R2x == 0 && (NYH * R1x) % nt == 0 &&
+           nt % R2y == 0 && NXH % (nt / R2y) == 0 && (NXH * R1y) % nt == 0;
+  }
+  static constexpr int pick() {
+    for (int nt = 256; nt >= 32; nt -= 32)
+      if (ok(nt)) return nt;
+    return 0;
+  }
+  static constexpr int NT = pick();
+  static_assert(NT > 0, "no thread count fits this half plane");
+  static constexpr int PX = NX + 8;     // x layout pitch (float2)
+  static constexpr int PY = NXH + 8;    // y layout pitch (float2)
+  static constexpr int BUF = (NYH * PX > NY * PY) ? NYH * PX : NY * PY;
+  static constexpr int JX1 = NYH * R2x / NT;
+  static constexpr int JX3 = NYH * R1x / NT;
+  static constexpr int CW = NT / R2y;
+  static constexpr int JY1 = NXH / CW;
+  static constexpr int JY3 = NXH * R1y / NT;
+  static constexpr size_t smem_bytes = sizeof(float2) * (size_t(BUF) + NX + NY);
+  static __device__ __forceinline__ int xphys(int r, int x) {
+    return r * PX + (x ^ ((x / R2x) & (R2x - 1)));
+  }
+  static __device__ __forceinline__ void x2_item(int t, int j, int& r, int& k1) {
+    const int lane = t & 31, w = t >> 5;
+    if constexpr (R1x == 16 && R2x == 8 && (NYH / 2) % (NT / 32) == 0) {
+      k1 = (lane & 7) + 8 * (lane >> 4);
+      r = 2 * (w + (NT / 32) * j) + ((lane >> 3) & 1);
+    } else if constexpr (R1x == 8 && R2x == 8 && (NYH / 4) % (NT / 32) == 0) {
+      k1 = lane & 7;
+      r = 4 * (w + (NT / 32) * j) + (lane >> 3);
+    } else {
+      const int q = t + NT * j;
+      r = q / R1x;
+      k1 = q % R1x;
+    }
+  }
+};
+
+template <int UBF16>
+__device__ __forceinline__ float2 load_u(const void* base, long long i) {
+  if constexpr (UBF16) {
+    const unsigned int raw = __ldcs(reinterpret_cast<const unsigned int*>(base) + i);
+    __nv_bfloat162 b = *reinterpret_cast<const __nv_bfloat162*>(&raw);
+    return __bfloat1622float2(b);
+  } else {
+    return __ldcs(reinterpret_cast<const float2*>(base) + i);
+  }
+}
+
+template <int NY, int NX, int MODE, int UBF16>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(XYCfg<NY, NX>::NT, 2)
+xy_kernel(const __grid_constant__ PassArgs a) {
+  using C = XYCfg<NY, NX>;
+  constexpr int R1x = C::R1x, R2x = C::R2x, R1y = C::R1y, R2y = C::R2y;
+  constexpr int NT = C::NT, NYH = C::NYH, NXH = C::NXH;
+  constexpr int DIR = (MODE == XY_FWD_REAL || MODE == XY_INV_SCORE) ? -1 : +1;
+
+  extern __shared__ __align__(16) float2 sm[];
+  float2* work = sm;
+  float2* twx = sm + C::BUF;
+  float2* twy = twx + NX;
+
+  const int t = threadIdx.x;
+  const int h = (int)cluster_rank();
+  const unsigned peer_base = map_cluster_rank(smem_addr(work), (unsigned)(h ^ 1));
+  const long long P = (long long)NY * NX;
+  const int cl = blockIdx.x >> 1, ncl = gridDim.x >> 1;
+  const int nsl = (MODE == XY_FWD_SCORE || MODE == XY_INV_SCORE) ? a.nslots : 1;
+  const int nunits = a.nz * nsl;
+
+  fill_twiddles<NX, DIR>(twx);
+  fill_twiddles<NY, DIR>(twy);
+  __syncthreads();
+
+  for (int u = cl; u < nunits; u += ncl) {
+    const int z = u % a.nz, s = u / a.nz;
+    const long long zoff = (long long)z * P;
+    // ---- x direction, step 1 on this CTA's rows (global -> registers -> shared)
+    {
+      long long ia, ib = -1;
+      if constexpr (MODE == XY_INV_SCORE) {
+        ia = a.ua[s];
+        ib = a.ub[s];
+      } else if constexpr (MODE == XY_FWD_SCORE) {
+        ia = (long long)s * a.slot_stride;
+      } else {
+        ia = a.in_off;
+      }
+      const int n2 = t % R2x, r0 = t / R2x;
+      float2 tw[R1x];
+#pragma unroll
+      for (int k1 = 0; k1 < R1x; ++k1) tw[k1] = twx[(n2 * k1) % NX];
+#pragma unroll
+      for (int j = 0; j < C::JX1; ++j) {
+        const int r = r0 + (NT / R2x) * j;
+        const long long row = zoff + (long long)(h * NYH + r) * NX;
+        float2 v[R1x];
+#pragma unroll
+        for (int n1 = 0; n1 < R1x; ++n1) {
+          const long long e = row + n2 + R2x * n1;
+          if constexpr (MODE == XY_FWD_REAL) {
+            v[n1] = make_float2(__ldg(reinterpret_cast<const float*>(a.in) + ia + e), 0.f);
+          } else if constexpr (MODE == XY_INV_SCORE) {
+            float2 q = load_u<UBF16>(a.in, ia + e);
+            if (ib >= 0) q = cadd(q, cconj(load_u<UBF16>(a.in, ib + e)));
+            v[n1] = q;
+          } else {
+            v[n1] = reinterpret_cast<const float2*>(a.in)[ia + e];
+          }
+        }
+        dft<R1x, DIR>(v);
+#pragma unroll
+        for (int k1 = 0; k1 < R1x; ++k1)
+          work[C::xphys(r, n2 + R2x * k1)] = (k1 == 0) ? v[k1] : cmul(v[k1], tw[k1]);
+      }
+    }
+    __syncthreads();
+    // ---- x direction, step 2; outputs go to the owner of their column
+    {
+      float2 w[C::JX3][R2x];
+#pragma unroll
+      for (int j = 0; j < C::JX3; ++j) {
+        int r, k1;
+        C::x2_item(t, j, r, k1);
+#pragma unroll
+        for (int m = 0; m < R2x; ++m) w[j][m] = work[C::xphys(r, m + R2x * k1)];
+        dft<R2x, DIR>(w[j]);
+      }
+      // both halves have read their x-layout buffers before either writes into
+      // the other's (release/acquire orders these reads before the peer's stores)
+      cluster_sync_acqrel();
+#pragma unroll
+      for (int j = 0; j < C::JX3; ++j) {
+        int r, k1;
+        C::x2_item(t, j, r, k1);
+        const int row = (h * NYH + r) * C::PY;
+#pragma unroll
+        for (int k2 = 0; k2 < R2x; ++k2) {
+          const int c = k1 + R1x * k2;
+          const int owner = (NXH % R1x == 0) ? (k2 >= NXH / R1x) : (c >= NXH);
+          const int idx = row + c - owner * NXH;
+          if (owner == h) work[idx] = w[j][k2];
+          else st_cluster_f2(peer_base + 8u * (unsigned)idx, w[j][k2]);
+        }
+      }
+      cluster_sync_acqrel();   // this CTA's y-layout buffer is complete
+    }
+    // ---- y direction, step 1 (in place)
+    {
+      const int n2 = t / C::CW;
+      float2 tw[R1y];
+#pragma unroll
+      for (int k1 = 0; k1 < R1y; ++k1) tw[k1] = twy[(n2 * k1) % NY];
+#pragma unroll
+      for (int j = 0; j < C::JY1; ++j) {
+        const int c = t % C::CW + C::CW * j;
+        float2 u1[R1y];
+#pragma unroll
+        for (int n1 = 0; n1 < R1y; ++n1) u1[n1] = work[(n2 + R2y * n1) * C::PY + c];
+        dft<R1y, DIR>(u1);
+#pragma unroll
+        for (int k1 = 0; k1 < R1y; ++k1)
+          work[(n2 + R2y * k1) * C::PY + c] = (k1 == 0) ? u1[k1] : cmul(u1[k1], tw[k1]);
+      }
+    }
+    __syncthreads();
+    // ---- y direction, step 2 + store
+    {
+      long long o, ob = -1;
+      if constexpr (MODE == XY_FWD_SCORE) {
+        o = a.ua[s];
+        ob = a.ub[s];
+      } else if constexpr (MODE == XY_INV_SCORE) {
+        o = (long long)s * a.slot_stride;
+      } else {
+        o = a.out_off;
+      }
+      const long long zo = zoff + h * NXH;
+#pragma unroll
+      for (int j = 0; j < C::JY3; ++j) {
+        const int q = t + NT * j;
+        const int c = q % NXH, k1 = q / NXH;
+        float2 w[R2y];
+#pragma unroll
+        for (int m = 0; m < R2y; ++m) w[m] = work[(m + R2y * k1) * C::PY + c];
+        dft<R2y, DIR>(w);
+#pragma unroll
+        for (int k2 = 0; k2 < R2y; ++k2) {
+          const long long e = zo + (long long)(k1 + R1y * k2) * NX + c;
+          if constexpr (MODE == XY_FWD_SCORE) {
+            store_u<UBF16>(a.out, o + e, w[k2]);
+            if (ob >= 0) store_u<UBF16>(a.out, ob + e, cconj(w[k2]));
+          } else if constexpr (MODE == XY_INV_REAL) {
+            reinterpret_cast<float*>(a.out)[o + e] = w[k2].x;
+          } else {
+            reinterpret_cast<float2*>(a.out)[o + e] = w[k2];
+          }
+        }
+      }
+    }
+    __syncthreads();    // work is rewritten by the next x step 1
+  }
+  cluster_sync_acqrel();   // no CTA leaves while its peer may still write into it
+}
+
+// ----------------------------------------------------------------------------
+// per-size launchers
+// ----------------------------------------------------------------------------
+template <int NZ>
+cudaError_t launch_z_n(int mode, int ev, const PassArgs& a, int tiles, cudaStream_t s) {
+  const dim3 block(kTileX * Plan<NZ>::R2);
+  switch (mode) {
+    case Z_FWD_PREP: z_kernel<NZ, Z_FWD_PREP, 0><<<tiles, block, 0, s>>>(a); break;
+    case Z_INV_FINAL: z_kernel<NZ, Z_INV_FINAL, 0><<<tiles, block, 0, s>>>(a); break;
+    case Z_FWD_SCORE:
+      if (ev == 0) z_kernel<NZ, Z_FWD_SCORE, 0><<<tiles, block, 0, s>>>(a);
+      else if (ev == 1) z_kernel<NZ, Z_FWD_SCORE, 1><<<tiles, block, 0, s>>>(a);
+      else z_kernel<NZ, Z_FWD_SCORE, 2><<<tiles, block, 0, s>>>(a);
+      break;
+    case Z_INV_SCORE:
+      if (ev == 0) z_kernel<NZ, Z_INV_SCORE, 0><<<tiles, block, 0, s>>>(a);
+      else if (ev == 1) z_kernel<NZ, Z_INV_SCORE, 1><<<tiles, block, 0, s>>>(a);
+      else z_kernel<NZ, Z_INV_SCORE, 2><<<tiles, block, 0, s>>>(a);
+      break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+template <int NY, int NX, int MODE, int UB>
+cudaError_t launch_xy_one(const PassArgs& a, cudaStream_t s) {
+  using C = XYCfg<NY, NX>;
+  auto k = xy_kernel<NY, NX, MODE, UB>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)C::smem_bytes);
+  if (e != cudaSuccess) return e;
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const int nsl = (MODE == XY_FWD_SCORE || MODE == XY_INV_SCORE) ? a.nslots : 1;
+  // two CTAs per SM, two per cluster: as many clusters as SMs, looping over units
+  const int clusters = std::max(1, std::min(a.nz * nsl, nsm));
+  k<<<2 * clusters, C::NT, C::smem_bytes, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <int NY, int NX>
+cudaError_t launch_xy_n(int mode, int ub, const PassArgs& a, cudaStream_t s) {
+  switch (mode) {
+    case XY_FWD_REAL: return launch_xy_one<NY, NX, XY_FWD_REAL, 0>(a, s);
+    case XY_INV_REAL: return launch_xy_one<NY, NX, XY_INV_REAL, 0>(a, s);
+    case XY_FWD_SCORE:
+      return ub ? launch_xy_one<NY, NX, XY_FWD_SCORE, 1>(a, s)
+                : launch_xy_one<NY, NX, XY_FWD_SCORE, 0>(a, s);
+    case XY_INV_SCORE:
+      return ub ? launch_xy_one<NY, NX, XY_INV_SCORE, 1>(a, s)
+                : launch_xy_one<NY, NX, XY_INV_SCORE, 0>(a, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace os3d
+
+// Per-size translation units instantiate these.
+#define OS3D_DEFINE_Z(N)                                                                   \
+  namespace os3d {                                                                         \
+  cudaError_t launch_z_##N(int mode, int ev, const PassArgs& a, int tiles, cudaStream_t s) { \
+    return launch_z_n<N>(mode, ev, a, tiles, s);                                           \
+  }                                                                                        \
+  }
+#define OS3D_DEFINE_XY(NY, NX)                                                             \
+  namespace os3d {                                                                         \
+  cudaError_t launch_xy_##NY##_##NX(int mode, int ub, const PassArgs& a, cudaStream_t s) {  \
+    return launch_xy_n<NY, NX>(mode, ub, a, s);                                            \
+  }                                                                                        \
+  }

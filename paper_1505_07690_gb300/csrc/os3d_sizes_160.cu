@@ -1,4 +1,3 @@
-// Instantiations of the z-pass for nz = 160 and the 128 x 160 xy-plane.
-#include "os3d_transform.cuh"
+// Instantiations of the z-pass for nz = 160.
+#include "os3d_passes.cuh"
 OS3D_DEFINE_Z(160)
-OS3D_DEFINE_XY(128, 160)

@@ -124,17 +124,23 @@ def test_inverse_and_adjoint_of_arbitrary_scores(M):
     assert rel(ga, O.adjoint(G[0].astype(np.complex128), ob)) <= TOL
 
 
-def test_batch_of_two(M):
+@pytest.mark.parametrize("bs", [0, 1, 3])
+def test_batch_of_two_repeated(M, bs):
+    """Two volumes per call, three calls in a row on one bank (consecutive
+    blocks run on two streams; a missing dependency shows up here)."""
     dims = (32, 32, 32)
-    bank, ob = _pair(M, dims, L=12)
+    bank, ob = _pair(M, dims, L=12, block_slots=bs)
     f = np.stack([synth.straight_tubes(dims, 3, seed=s) for s in (11, 12)])
-    U = M.os3d_forward(bank, _cuda(f))
-    Ug = _to_np(U)
-    fr = _to_np(M.os3d_inverse(bank, U))
-    for b in range(2):
-        Uo = O.forward(f[b], ob)
-        assert rel(Ug[b], Uo) <= TOL
-        assert rel(fr[b], O.inverse(Uo, ob)) <= TOL
+    Uo = [O.forward(f[b], ob) for b in range(2)]
+    fo = [O.inverse(Uo[b], ob) for b in range(2)]
+    fd = _cuda(f)
+    for _ in range(3):
+        U = M.os3d_forward(bank, fd)
+        fr = M.os3d_inverse(bank, U)
+        Ug, frg = _to_np(U), _to_np(fr)
+        for b in range(2):
+            assert rel(Ug[b], Uo[b]) <= TOL
+            assert rel(frg[b], fo[b]) <= TOL
 
 
 def test_bf16_storage(M):
