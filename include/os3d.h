@@ -146,6 +146,30 @@ os3d_status os3d_bank_minv(const os3d_bank* bank, float* minv, void* stream);
 os3d_status os3d_destroy_bank(os3d_bank* bank);
 const char* os3d_status_string(os3d_status s);
 
+/* ---- forward transform without a workspace (no counterpart in the paper) --
+ * os3d_forward_static computes exactly what os3d_forward computes, but keeps
+ * all of its scratch in a fixed array inside the library instead of a
+ * workspace, and allocates nothing: no cudaMalloc, cudaFree or allocating
+ * library call. It is meant for callers that cannot allocate device memory
+ * when they run the transform (device memory owned by a framework's pool
+ * allocator that may not be bypassed; latency-critical loops where a
+ * cudaMalloc, which can synchronise the device, is not acceptable). The bank
+ * itself is still made beforehand by os3d_make_wavelets.
+ * Limits: volumes of at most OS3D_STATIC_MAX_VOXELS voxels (64^3); larger
+ * banks are rejected with OS3D_EINVAL. The array (3 x OS3D_STATIC_MAX_VOXELS
+ * complex floats, 6 MiB) is held by every GPU that loads the library until
+ * the process exits. The first call on each device looks up the array's
+ * device address (cudaGetSymbolAddress) with that device current; make that
+ * first call before any stream capture. All calls share the one array and it
+ * keeps the last call's contents (every element is overwritten before it is
+ * read, so nothing needs clearing); calls that overlap on the GPU (other
+ * streams, other threads) race on it and must be serialised by the caller.
+ * Orientation pairs are processed one at a time on `stream` (no side
+ * streams). Arguments and errors otherwise as os3d_forward. */
+#define OS3D_STATIC_MAX_VOXELS (64 * 64 * 64)
+os3d_status os3d_forward_static(const os3d_bank* bank, const float* f, int batch, void* U,
+                                os3d_udtype udtype, void* stream);
+
 
 /* ---- diagnostics (no counterpart in the paper) ---------------------------
  * Kernel kinds of the transform: the xy-passes (2D DFT of one z-plane with

@@ -814,6 +814,101 @@ os3d_status os3d_adjoint(const os3d_bank* b, const void* G, os3d_udtype udtype, 
 
 }  // extern "C"
 
+// ===========================================================================
+// Forward transform with its scratch in a fixed static device array.
+//
+// For callers that cannot allocate device memory when they run the
+// transform: a process whose device memory belongs to a framework's pool
+// allocator it may not bypass, or a latency-critical loop in which a
+// cudaMalloc (which can synchronise the device) is not acceptable. The
+// scratch lives in g_static_scratch below, a file-scope __device__ array of
+// OS3D_STATIC_MAX_VOXELS x 3 complex values (6 MiB) that every GPU which
+// loads this library holds until the process exits. Its device address is
+// looked up once per device, on the first call made with that device
+// current; that first call must therefore come before any stream capture.
+// ===========================================================================
+namespace {
+
+constexpr long long kStaticMaxVoxels = OS3D_STATIC_MAX_VOXELS;
+// f_hat, one per-volume intermediate and one block intermediate (one pair)
+static __device__ __align__(256) float2 g_static_scratch[3 * kStaticMaxVoxels];
+
+constexpr int kStaticMaxDevices = 64;
+std::mutex g_static_mu;
+void* g_static_ptr[kStaticMaxDevices] = {};
+
+// device address of g_static_scratch on the current device
+os3d_status static_scratch_address(float2** out) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kStaticMaxDevices)
+    return OS3D_ECUDA;
+  std::lock_guard<std::mutex> lk(g_static_mu);
+  if (!g_static_ptr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess || !p) {
+      cudaGetLastError();
+      return OS3D_ECUDA;
+    }
+    g_static_ptr[dev] = p;
+  }
+  *out = static_cast<float2*>(g_static_ptr[dev]);
+  return OS3D_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+os3d_status os3d_forward_static(const os3d_bank* b, const float* f, int batch, void* U,
+                                os3d_udtype udtype, void* stream) {
+  const os3d_status st = check_call(b, f, U, batch, udtype, nullptr);
+  if (st != OS3D_OK) return st;
+  if (b->nvox > kStaticMaxVoxels) return OS3D_EINVAL;   // larger than the static scratch
+  float2* scratch = nullptr;
+  const os3d_status sa = static_scratch_address(&scratch);
+  if (sa != OS3D_OK) return sa;
+  // every scratch element is written before it is read within a call, so no
+  // clearing is needed between calls
+  float2* fh = scratch;
+  float2* T0 = scratch + b->nvox;
+  float2* T = scratch + 2 * b->nvox;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int nz = b->dims[0], ny = b->dims[1], nx = b->dims[2];
+  const int nslots = (int)b->slot_a.size();
+  const int tiles = ny * (nx / kTileX);
+  const long long n = b->nvox;
+  for (int v = 0; v < batch; ++v) {
+    PassArgs x0 = args_base(b);
+    x0.in = f;
+    x0.in_off = (long long)v * n;
+    x0.out = T0;
+    OS3D_CK(counted_launch(OS3D_KIND_XY_FWD_REAL, s,
+                           [&] { return launch_xy(ny, nx, XY_FWD_REAL, 0, x0, s); }));
+    PassArgs zp = args_base(b);
+    zp.in = T0;
+    zp.out = fh;
+    zp.mult = b->Gs;
+    OS3D_CK(counted_launch(OS3D_KIND_Z_FWD_PREP, s,
+                           [&] { return launch_z(nz, Z_FWD_PREP, 0, zp, tiles, s); }));
+    for (int s0 = 0; s0 < nslots; ++s0) {   // one orientation pair at a time
+      PassArgs za = args_base(b);
+      set_slots(b, za, v, s0, 1);
+      za.in = fh;
+      za.out = T;
+      OS3D_CK(counted_launch(OS3D_KIND_Z_FWD_SCORE, s,
+                             [&] { return launch_z(nz, Z_FWD_SCORE, b->ev, za, tiles, s); }));
+      PassArgs xa = za;
+      xa.in = T;
+      xa.out = U;
+      OS3D_CK(counted_launch(OS3D_KIND_XY_FWD_SCORE, s,
+                             [&] { return launch_xy(ny, nx, XY_FWD_SCORE, udtype, xa, s); }));
+    }
+  }
+  return OS3D_OK;
+}
+
+}  // extern "C"
+
 extern "C" {
 
 unsigned long long os3d_launch_count(void) { return g_launches.load(); }

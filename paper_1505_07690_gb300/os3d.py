@@ -64,12 +64,14 @@ def lib():
         L.os3d_profile_enable.argtypes = [i]
         L.os3d_profile_read.argtypes = [i, ctypes.POINTER(ctypes.c_ulonglong), ctypes.POINTER(d)]
         L.os3d_profile_reset.argtypes = []
+        L.os3d_forward_static.argtypes = [vp, vp, i, vp, i, vp]
         L.os3d_kernel_kind_name.restype = ctypes.c_char_p
         L.os3d_kernel_kind_name.argtypes = [i]
         for name in ("os3d_default_params", "os3d_icosa_orientations", "os3d_make_wavelets",
                      "os3d_forward", "os3d_inverse", "os3d_adjoint", "os3d_bank_info",
                      "os3d_bank_coefficients", "os3d_bank_minv", "os3d_destroy_bank",
-                     "os3d_profile_enable", "os3d_profile_read", "os3d_profile_reset"):
+                     "os3d_profile_enable", "os3d_profile_read", "os3d_profile_reset",
+                     "os3d_forward_static"):
             getattr(L, name).restype = i
         _lib = L
     return _lib
@@ -217,6 +219,25 @@ def os3d_forward(bank: Bank, f, U=None, bf16: bool = False, workspace=None, stre
         raise ValueError("batch of U and f differ")
     _check(lib().os3d_forward(bank.handle, _ptr(f), batch, _ptr(U), ud, _ws_ptr(workspace),
                               _stream(stream)), "os3d_forward")
+    return U
+
+
+def os3d_forward_static(bank: Bank, f, U=None, bf16: bool = False, stream=None):
+    """os3d_forward with the scratch in the library's fixed static device array
+    instead of a workspace: allocates no device memory itself (U is
+    allocated here only when the caller passes none). For volumes of at most
+    64^3 voxels; concurrent calls race on the shared array."""
+    import torch
+    if not (f.is_cuda and f.dtype == torch.float32 and f.is_contiguous()):
+        raise ValueError("f must be a contiguous float32 CUDA tensor")
+    batch = _batch_of(f, 3, bank.dims)
+    if U is None:
+        U = new_score(bank, batch, bf16)
+    ud, ub = _check_score(bank, U)
+    if ub != batch:
+        raise ValueError("batch of U and f differ")
+    _check(lib().os3d_forward_static(bank.handle, _ptr(f), batch, _ptr(U), ud, _stream(stream)),
+           "os3d_forward_static")
     return U
 
 
