@@ -72,7 +72,7 @@ typedef struct {
   double eps;       /* clamp M -> max(M, eps) of the inverse, eps > 0                */
   int fit_mode;     /* 1: least squares on the order-15 icosahedral tessellation
                        (the paper's pseudo-inverse); 0: L2 projection (Gauss-Legendre) */
-  int block_slots;  /* orientation pairs per launch block, 0 = automatic, else 1..8  */
+  int block_slots;  /* orientation pairs per launch block, 0 = automatic (8), else 1..8 */
 } os3d_params;
 
 typedef struct os3d_bank os3d_bank; /* opaque, library-owned */
