@@ -24,12 +24,33 @@ namespace os3d {
 #define OS3D_DECL_XY(NY, NX) \
   cudaError_t launch_xy_##NY##_##NX(int, int, const PassArgs&, cudaStream_t);
 OS3D_DECL_Z(16) OS3D_DECL_Z(32) OS3D_DECL_Z(48) OS3D_DECL_Z(64) OS3D_DECL_Z(96)
-OS3D_DECL_Z(128) OS3D_DECL_Z(160)
+OS3D_DECL_Z(128) OS3D_DECL_Z(160) OS3D_DECL_Z(256)
 OS3D_DECL_XY(16, 16) OS3D_DECL_XY(32, 32) OS3D_DECL_XY(48, 48) OS3D_DECL_XY(64, 64)
 OS3D_DECL_XY(96, 96) OS3D_DECL_XY(128, 128)
+#define OS3D_DECL_PN(N)                                                                   \
+  cudaError_t launch_pencil_##N(int, int, int, const PassArgs&, const PencilGeom&, long long, \
+                                int, cudaStream_t);
+OS3D_DECL_PN(16) OS3D_DECL_PN(32) OS3D_DECL_PN(48) OS3D_DECL_PN(64) OS3D_DECL_PN(96)
+OS3D_DECL_PN(128) OS3D_DECL_PN(160) OS3D_DECL_PN(256)
+
+cudaError_t launch_pencil(int n, int mode, int dir, int ub, const PassArgs& a, const PencilGeom& g,
+                          long long nlines, int nslots, cudaStream_t s) {
+  switch (n) {
+    case 16: return launch_pencil_16(mode, dir, ub, a, g, nlines, nslots, s);
+    case 32: return launch_pencil_32(mode, dir, ub, a, g, nlines, nslots, s);
+    case 48: return launch_pencil_48(mode, dir, ub, a, g, nlines, nslots, s);
+    case 64: return launch_pencil_64(mode, dir, ub, a, g, nlines, nslots, s);
+    case 96: return launch_pencil_96(mode, dir, ub, a, g, nlines, nslots, s);
+    case 128: return launch_pencil_128(mode, dir, ub, a, g, nlines, nslots, s);
+    case 160: return launch_pencil_160(mode, dir, ub, a, g, nlines, nslots, s);
+    case 256: return launch_pencil_256(mode, dir, ub, a, g, nlines, nslots, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
 
 bool z_supported(int nz) {
-  return nz == 16 || nz == 32 || nz == 48 || nz == 64 || nz == 96 || nz == 128 || nz == 160;
+  return nz == 16 || nz == 32 || nz == 48 || nz == 64 || nz == 96 || nz == 128 || nz == 160 ||
+         nz == 256;
 }
 bool xy_supported(int ny, int nx) {
   return ny == nx && (nx == 16 || nx == 32 || nx == 48 || nx == 64 || nx == 96 || nx == 128);
@@ -43,6 +64,7 @@ cudaError_t launch_z(int nz, int mode, int ev, const PassArgs& a, int tiles, cud
     case 96: return launch_z_96(mode, ev, a, tiles, s);
     case 128: return launch_z_128(mode, ev, a, tiles, s);
     case 160: return launch_z_160(mode, ev, a, tiles, s);
+    case 256: return launch_z_256(mode, ev, a, tiles, s);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -418,7 +440,7 @@ os3d_status os3d_make_wavelets(const int dims[3], const double* orient, int n_o,
   }
   const int nz = dims[0], ny = dims[1], nx = dims[2];
   if (nz < 1 || ny < 1 || nx < 1) return OS3D_EINVAL;
-  if (!axis_ok(nz) || !xy_supported(ny, nx) || nx % kTileX) return OS3D_EUNSUPPORTED;
+  if (!axis_ok(nz) || !axis_ok(ny) || !axis_ok(nx) || nx % kTileX) return OS3D_EUNSUPPORTED;
   if (fault_is("alloc")) return OS3D_ENOMEM;
   cudaStream_t s = (cudaStream_t)stream;
 
@@ -698,6 +720,45 @@ os3d_status check_call(const os3d_bank* b, const void* x, const void* y, int bat
     if ((call) != cudaSuccess) return OS3D_ECUDA; \
   } while (0)
 
+// One xy-pass of `mode`: the cluster kernel when a z-plane fits it, otherwise
+// a pencil pass along x and one along y (the y pass in place on complex data).
+cudaError_t launch_plane(const os3d_bank* b, int mode, int ub, const PassArgs& a, cudaStream_t s) {
+  const int nz = b->dims[0], ny = b->dims[1], nx = b->dims[2];
+  if (xy_supported(ny, nx)) return launch_xy(ny, nx, mode, ub, a, s);
+  const long long P = (long long)ny * nx;
+  const PencilGeom gx{ny, P, nx, 1};    // lines = rows, elements contiguous
+  const PencilGeom gy{nx, P, 1, nx};    // lines = columns, elements nx apart
+  const long long lx = (long long)nz * ny, ly = (long long)nz * nx;
+  const int ns = (mode == XY_FWD_SCORE || mode == XY_INV_SCORE) ? a.nslots : 1;
+  PassArgs c = a;   // complex work array for the in-place y pass
+  cudaError_t e;
+  switch (mode) {
+    case XY_FWD_REAL:   // f -> DFT_x -> out, then DFT_y in place
+      e = launch_pencil(nx, PN_R2C, -1, 0, a, gx, lx, 1, s);
+      if (e != cudaSuccess) return e;
+      c.in = a.out;
+      c.in_off = a.out_off;
+      return launch_pencil(ny, PN_C2C, -1, 0, c, gy, ly, 1, s);
+    case XY_INV_REAL:   // IDFT_y in place on in, then IDFT_x -> real out
+      c.out = const_cast<void*>(a.in);
+      c.out_off = a.in_off;
+      e = launch_pencil(ny, PN_C2C, 1, 0, c, gy, ly, 1, s);
+      if (e != cudaSuccess) return e;
+      return launch_pencil(nx, PN_C2R, 1, 0, a, gx, lx, 1, s);
+    case XY_FWD_SCORE:  // IDFT_y in place on T_s, then IDFT_x -> U_a, U_b
+      c.out = const_cast<void*>(a.in);
+      e = launch_pencil(ny, PN_C2C, 1, 0, c, gy, ly, ns, s);
+      if (e != cudaSuccess) return e;
+      return launch_pencil(nx, PN_C2U, 1, ub, a, gx, lx, ns, s);
+    case XY_INV_SCORE:  // U_a + conj U_b -> DFT_x -> T_s, then DFT_y in place
+      e = launch_pencil(nx, PN_U2C, -1, ub, a, gx, lx, ns, s);
+      if (e != cudaSuccess) return e;
+      c.in = a.out;
+      return launch_pencil(ny, PN_C2C, -1, 0, c, gy, ly, ns, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 // inverse (use_m = true) or adjoint (use_m = false). Consecutive blocks of
 // orientation pairs alternate between the two side streams (each with its own
 // intermediates and partial sum), so one block's xy-pass overlaps the other's
@@ -721,7 +782,7 @@ os3d_status backward_impl(const os3d_bank* b, const void* U, int udtype, int bat
       xa.in = U;
       xa.out = w.T[k];
       OS3D_CK(counted_launch(OS3D_KIND_XY_INV_SCORE, st,
-                             [&] { return launch_xy(ny, nx, XY_INV_SCORE, udtype, xa, st); }));
+                             [&] { return launch_plane(b, XY_INV_SCORE, udtype, xa, st); }));
       PassArgs za = xa;
       za.in = w.T[k];
       za.out = w.A[k];
@@ -742,7 +803,7 @@ os3d_status backward_impl(const os3d_bank* b, const void* U, int udtype, int bat
     xf.out = fout;
     xf.out_off = (long long)v * n;
     OS3D_CK(counted_launch(OS3D_KIND_XY_INV_REAL, s,
-                           [&] { return launch_xy(ny, nx, XY_INV_REAL, 0, xf, s); }));
+                           [&] { return launch_plane(b, XY_INV_REAL, 0, xf, s); }));
   }
   return OS3D_OK;
 }
@@ -768,7 +829,7 @@ os3d_status os3d_forward(const os3d_bank* b, const float* f, int batch, void* U,
     x0.in_off = (long long)v * n;
     x0.out = w.T0;
     OS3D_CK(counted_launch(OS3D_KIND_XY_FWD_REAL, s,
-                           [&] { return launch_xy(ny, nx, XY_FWD_REAL, 0, x0, s); }));
+                           [&] { return launch_plane(b, XY_FWD_REAL, 0, x0, s); }));
     PassArgs zp = args_base(b);
     zp.in = w.T0;
     zp.out = w.fh;
@@ -792,7 +853,7 @@ os3d_status os3d_forward(const os3d_bank* b, const float* f, int batch, void* U,
       xa.in = w.T[k];
       xa.out = U;
       OS3D_CK(counted_launch(OS3D_KIND_XY_FWD_SCORE, st,
-                             [&] { return launch_xy(ny, nx, XY_FWD_SCORE, udtype, xa, st); }));
+                             [&] { return launch_plane(b, XY_FWD_SCORE, udtype, xa, st); }));
     }
     OS3D_CK(join_side(b, s));
   }
@@ -884,7 +945,7 @@ os3d_status os3d_forward_static(const os3d_bank* b, const float* f, int batch, v
     x0.in_off = (long long)v * n;
     x0.out = T0;
     OS3D_CK(counted_launch(OS3D_KIND_XY_FWD_REAL, s,
-                           [&] { return launch_xy(ny, nx, XY_FWD_REAL, 0, x0, s); }));
+                           [&] { return launch_plane(b, XY_FWD_REAL, 0, x0, s); }));
     PassArgs zp = args_base(b);
     zp.in = T0;
     zp.out = fh;
@@ -902,7 +963,7 @@ os3d_status os3d_forward_static(const os3d_bank* b, const float* f, int batch, v
       xa.in = T;
       xa.out = U;
       OS3D_CK(counted_launch(OS3D_KIND_XY_FWD_SCORE, s,
-                             [&] { return launch_xy(ny, nx, XY_FWD_SCORE, udtype, xa, s); }));
+                             [&] { return launch_plane(b, XY_FWD_SCORE, udtype, xa, s); }));
     }
   }
   return OS3D_OK;

@@ -189,6 +189,7 @@ template <> struct Plan<64>  { static constexpr int R1 = 8,  R2 = 8; };
 template <> struct Plan<96>  { static constexpr int R1 = 12, R2 = 8; };
 template <> struct Plan<128> { static constexpr int R1 = 16, R2 = 8; };
 template <> struct Plan<160> { static constexpr int R1 = 20, R2 = 8; };
+template <> struct Plan<256> { static constexpr int R1 = 16, R2 = 16; };
 
 // Twiddle table W_N^m = exp(DIR 2 pi i m / N), m < N, in shared memory.
 template <int N, int DIR>

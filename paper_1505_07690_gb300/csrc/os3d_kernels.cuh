@@ -51,6 +51,21 @@ struct PassArgs {
   HEval h;
 };
 
+// Strided pencil passes (x and y directions of planes that the xy-pass
+// cannot hold): modes and line geometry, see os3d_pencil.cuh.
+enum PencilMode {
+  PN_C2C = 0,   // complex -> complex (in place allowed); blockIdx.y = slot
+  PN_R2C = 1,   // real f -> complex (forward DFT)
+  PN_C2R = 2,   // complex -> real part (inverse DFT)
+  PN_C2U = 3,   // T_s -> U_a and U_b = conj U_a (inverse DFT)
+  PN_U2C = 4    // U_a + conj U_b -> T_s (forward DFT)
+};
+
+struct PencilGeom {
+  int group;
+  long long gstride, lstride, estride;
+};
+
 // launchers (return cudaGetLastError of the launch)
 cudaError_t launch_z(int nz, int mode, int ev, const PassArgs& a, int grid_tiles,
                      cudaStream_t s);

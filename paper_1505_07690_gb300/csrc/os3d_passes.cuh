@@ -96,7 +96,7 @@ __device__ __forceinline__ unsigned cluster_rank() {
 // z-pass: DFT along z of a 16-wide pencil tile (all slots of the block)
 // ----------------------------------------------------------------------------
 template <int NZ, int MODE, int EV>
-__global__ void __launch_bounds__(kTileX * Plan<NZ>::R2, 4)
+__global__ void __launch_bounds__(kTileX * Plan<NZ>::R2, Plan<NZ>::R2 >= 16 ? 2 : 4)
 z_kernel(const __grid_constant__ PassArgs a) {
   constexpr int R1 = Plan<NZ>::R1, R2 = Plan<NZ>::R2;
   constexpr int TW = kTileX;

@@ -201,3 +201,34 @@ def test_headline_size_sampled(M):
     ball = np.sqrt(wz ** 2 + wy ** 2 + wx ** 2) < np.pi
     fb = np.fft.ifftn(fhat * ball).real
     assert rel(fr, fb) <= TOL
+
+
+@pytest.mark.parametrize("dims,subdiv", [((32, 48, 64), 1), ((32, 256, 16), 0), ((16, 160, 32), 1),
+                                         ((256, 32, 32), 0)])
+def test_pencil_path_grids(M, dims, subdiv):
+    """Grids whose z-planes are not square planes of side <= 128 run the x and
+    y directions as separate pencil passes (and 256 along any axis)."""
+    f = synth.straight_tubes(dims, 2, seed=8, noise=0.1)
+    _check_forward_inverse(M, dims, f, subdiv=subdiv, L=12, block_slots=4)
+
+
+def test_precision_workload_sampled_c64_and_bf16(M):
+    """256^3, 40 spline tubes, 42 orientations, L = 20: complex64 scores match
+    the oracle on sampled orientations; both storage formats reconstruct
+    W^-1 W f = IDFT[1_ball f_hat] (complex64 within 1e-5, bf16 within 5e-3)."""
+    import torch
+    dims = (256, 256, 256)
+    f = synth.workload_volume("splines256_no42")
+    bank, ob = _pair(M, dims, subdiv=1, L=20)
+    fd = _cuda(f)
+    fhat = np.fft.fftn(f.astype(np.float64))
+    wz, wy, wx = O.freq_grid(dims)
+    fb = np.fft.ifftn(fhat * (np.sqrt(wz ** 2 + wy ** 2 + wx ** 2) < np.pi)).real
+    U = M.os3d_forward(bank, fd)
+    for i in (0, 29):
+        assert rel(_to_np(U[0, i]), O.forward_one(fhat, ob, i)) <= TOL, i
+    assert rel(_to_np(M.os3d_inverse(bank, U))[0], fb) <= TOL
+    del U
+    torch.cuda.empty_cache()
+    Ub = M.os3d_forward(bank, fd, bf16=True)
+    assert rel(_to_np(M.os3d_inverse(bank, Ub))[0], fb) <= TOL_BF16
