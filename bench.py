@@ -45,6 +45,11 @@ def _args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--block-slots", type=int, default=0,
                     help="orientation pairs per launch block (0 = the library's choice)")
+    ap.add_argument("--serve", type=int, default=0,
+                    help="instead of the headline: serve this many Poisson-arriving requests "
+                         "of the mixed-size workload and report p50/p99 latency")
+    ap.add_argument("--load", type=float, default=0.8,
+                    help="--serve arrival rate as a fraction of the measured capacity")
     ap.add_argument("--workload", default=WORKLOAD,
                     help="named synthetic workload (default: the 128^3 x 162 headline)")
     return ap.parse_args()
@@ -364,12 +369,95 @@ def run_ours(args):
     return 0
 
 
+# ---------------------------------------------------------------------------
+# serving: mixed sizes and orientation counts, Poisson arrivals
+# ---------------------------------------------------------------------------
+SERVE_SHAPES = [(48, 48, 48), (64, 64, 64), (96, 96, 96), (128, 128, 128), (96, 128, 160)]
+SERVE_SUBDIVS = [1, 2]   # 42 or 162 orientations
+
+
+def run_serve(args):
+    import numpy as np
+    import torch
+    from paper_1505_07690_gb300 import build, os3d, synth
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    build.build()
+    rng = np.random.default_rng(rank)
+    # volume pool: 2 seeded spline-tube volumes per shape (volume seed 1000 + k)
+    pool = {sh: [torch.from_numpy(synth.spline_tubes(sh, 6, seed=1000 + k, noise=0.2)).pin_memory()
+                 for k in range(2)] for sh in SERVE_SHAPES}
+    reqs = [(SERVE_SHAPES[rng.integers(len(SERVE_SHAPES))], SERVE_SUBDIVS[rng.integers(2)],
+             int(rng.integers(2))) for _ in range(args.serve)]
+    n_o = {1: 42, 2: 162}
+    vo = [int(np.prod(sh)) * n_o[sd] for sh, sd, _ in reqs]
+    srv = os3d.Server(os3d.os3d_server_default_config(arena_bytes=24 << 30, max_inflight=4,
+                                                      udtype=1 if args.bf16 else 0),
+                      os3d.os3d_default_params(L=16))
+
+    def drain(outstanding, lat, block):
+        while outstanding:
+            try:
+                _, l = srv.wait(outstanding[0], 600.0 if block else 0.0)
+            except os3d.OS3DError as e:
+                if e.status == 4:
+                    return
+                raise
+            lat.append(l)
+            outstanding.pop(0)
+
+    # banks for every (shape, orientation set), outside the timed part
+    warm = [srv.submit(pool[sh][0], sd) for sh in SERVE_SHAPES for sd in SERVE_SUBDIVS]
+    for t in warm:
+        srv.wait(t, 600.0)
+    # capacity: all requests queued at once (closed loop)
+    t0 = time.perf_counter()
+    out, lat = [], []
+    for sh, sd, k in reqs:
+        out.append(srv.submit(pool[sh][k], sd))
+        drain(out, lat, False)
+    drain(out, lat, True)
+    t_cap = time.perf_counter() - t0
+    capacity = len(reqs) / t_cap
+    # Poisson arrivals at load x capacity
+    rate = args.load * capacity
+    gaps = rng.exponential(1.0 / rate, len(reqs))
+    out, lat = [], []
+    t0 = time.perf_counter()
+    t_next = t0
+    for (sh, sd, k), g in zip(reqs, gaps):
+        t_next += g
+        while time.perf_counter() < t_next:
+            drain(out, lat, False)
+            time.sleep(min(2e-4, max(0.0, t_next - time.perf_counter())))
+        out.append(srv.submit(pool[sh][k], sd))
+    drain(out, lat, True)
+    t_run = time.perf_counter() - t0
+    srv.close()
+    line = {
+        "metric": "serving: forward+inverse per request, mixed sizes, Poisson arrivals; p50/p99 latency",
+        "value": sum(vo) / t_run, "unit": UNIT, "n_gpus": 1, "higher_is_better": True,
+        "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                       "mean": float(np.mean(lat))},
+        "requests": len(reqs), "requests_per_s": len(reqs) / t_run,
+        "capacity_requests_per_s": capacity, "load": args.load,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "serve_mix", "shapes": SERVE_SHAPES, "n_o": [42, 162], "L": 16,
+                   "arrival": "poisson", "udtype": "bf16x2" if args.bf16 else "c64",
+                   "max_inflight": 4, "arena_gb": 24},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     global WORKLOAD
     args = _args()
     WORKLOAD = args.workload
     if args.impl == "reference":
         return run_reference(args)
+    if args.serve:
+        return run_serve(args)
     return run_ours(args)
 
 

@@ -73,12 +73,15 @@ typedef struct {
   int fit_mode;     /* 1: least squares on the order-15 icosahedral tessellation
                        (the paper's pseudo-inverse); 0: L2 projection (Gauss-Legendre) */
   int block_slots;  /* orientation pairs per launch block, 0 = automatic (8), else 1..8 */
+  int overlap;      /* 1: consecutive blocks alternate between two internal streams of the
+                       bank (forked from and joined to the caller's stream); 0: every launch
+                       on the caller's stream (for callers running many transforms at once) */
 } os3d_params;
 
 typedef struct os3d_bank os3d_bank; /* opaque, library-owned */
 
 /* Defaults: k = 2, s_theta = 0.7, L = 16, N = 8, gamma = 0.8, eps = 1e-4,
- * fit_mode = 1, block_slots = 0. Host only. */
+ * fit_mode = 1, block_slots = 0, overlap = 1. Host only. */
 os3d_status os3d_default_params(os3d_params* p);
 
 /* Orientation set of Sec. 2.1: an icosahedron (vertices: cyclic permutations
@@ -146,6 +149,47 @@ os3d_status os3d_bank_minv(const os3d_bank* bank, float* minv, void* stream);
 
 os3d_status os3d_destroy_bank(os3d_bank* bank);
 const char* os3d_status_string(os3d_status s);
+
+/* ---- serving (no counterpart in the paper) --------------------------------
+ * A server owns a device arena of arena_bytes, allocated once at creation, and
+ * a worker thread. Each request is one host volume f (nz*ny*nx floats) with
+ * the icosahedral orientation set of `subdiv` subdivisions: the server copies
+ * f to the device, runs os3d_forward into a score held in the arena, then
+ * os3d_inverse, and copies the reconstruction to f_out (host). Requests are
+ * admitted in arrival order as soon as one of max_inflight stream slots and
+ * the request's footprint (score + two images + workspace) in the arena are
+ * free; admitted requests run concurrently. Wavelet banks are made on first
+ * use per (grid, orientation set) with the server's parameters and kept until
+ * os3d_server_destroy. f and f_out must stay valid until the request is
+ * complete and should be page-locked (pageable host memory makes the copies,
+ * and with them the worker thread, synchronous). The server must be created,
+ * used and destroyed with one device current. */
+typedef struct {
+  size_t arena_bytes;  /* device memory for in-flight requests                  */
+  int max_inflight;    /* concurrent requests (streams), 1..64                  */
+  int udtype;          /* score storage of every request: OS3D_U_C64 or BF16X2  */
+} os3d_server_config;
+typedef struct os3d_server os3d_server;
+
+/* arena_bytes = 16 GiB, max_inflight = 4, udtype = OS3D_U_C64. Host only. */
+os3d_status os3d_server_default_config(os3d_server_config* cfg);
+/* Errors: EINVAL (config out of range), ENOMEM (arena), ECUDA. p may be NULL
+ * (defaults). */
+os3d_status os3d_server_create(const os3d_server_config* cfg, const os3d_params* p,
+                               os3d_server** out);
+/* Queues a request and returns its ticket at once. EINVAL for bad arguments;
+ * a grid without a plan or a request larger than the arena completes with
+ * that status (EUNSUPPORTED, ENOMEM) instead. */
+os3d_status os3d_server_submit(os3d_server* s, const int dims[3], int subdiv, const float* f,
+                               float* f_out, long long* ticket);
+/* Waits at most timeout_s seconds for the request: OS3D_ETIMEOUT if it is not
+ * complete by then (the ticket stays valid), else the request's status; then
+ * *latency_ms (may be NULL) is the time from submission to completion and the
+ * ticket is released. */
+os3d_status os3d_server_wait(os3d_server* s, long long ticket, double timeout_s,
+                             double* latency_ms);
+/* Finishes every queued and in-flight request, then frees the server. */
+os3d_status os3d_server_destroy(os3d_server* s);
 
 /* ---- forward transform without a workspace (no counterpart in the paper) --
  * os3d_forward_static computes exactly what os3d_forward computes, but keeps

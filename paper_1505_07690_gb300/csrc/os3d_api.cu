@@ -311,7 +311,7 @@ bool axis_ok(int n) { return z_supported(n); }
 os3d_status check_params(const os3d_params& p) {
   if (p.k < 0 || p.k > 8 || !(p.s_theta > 0.0) || p.L < 0 || p.L > kMaxL || p.N < 0 || p.N > 64 ||
       !(p.gamma > 0.0 && p.gamma < 1.0) || !(p.eps > 0.0) || (p.fit_mode != 0 && p.fit_mode != 1) ||
-      p.block_slots < 0 || p.block_slots > kMaxSlots)
+      p.block_slots < 0 || p.block_slots > kMaxSlots || (p.overlap != 0 && p.overlap != 1))
     return OS3D_EINVAL;
   return OS3D_OK;
 }
@@ -406,6 +406,7 @@ os3d_status os3d_default_params(os3d_params* p) {
   p->eps = 1e-4;
   p->fit_mode = 1;
   p->block_slots = 0;
+  p->overlap = 1;
   return OS3D_OK;
 }
 
@@ -771,12 +772,12 @@ os3d_status backward_impl(const os3d_bank* b, const void* U, int udtype, int bat
   const int tiles = ny * (nx / kTileX);
   const long long n = b->nvox;
   for (int v = 0; v < batch; ++v) {
-    OS3D_CK(fork_side(b, s));
+    if (b->p.overlap) OS3D_CK(fork_side(b, s));
     int q = 0;
     for (int s0 = 0; s0 < nslots; s0 += b->block_slots, ++q) {
       const int ns = std::min(b->block_slots, nslots - s0);
-      const int k = q & 1;
-      cudaStream_t st = b->side[k];
+      const int k = b->p.overlap ? (q & 1) : 0;
+      cudaStream_t st = b->p.overlap ? b->side[k] : s;
       PassArgs xa = args_base(b);
       set_slots(b, xa, v, s0, ns);
       xa.in = U;
@@ -786,14 +787,14 @@ os3d_status backward_impl(const os3d_bank* b, const void* U, int udtype, int bat
       PassArgs za = xa;
       za.in = w.T[k];
       za.out = w.A[k];
-      za.accumulate = q >= 2;
+      za.accumulate = b->p.overlap ? q >= 2 : q >= 1;
       OS3D_CK(counted_launch(OS3D_KIND_Z_INV_SCORE, st,
                              [&] { return launch_z(nz, Z_INV_SCORE, b->ev, za, tiles, st); }));
     }
-    OS3D_CK(join_side(b, s));
+    if (b->p.overlap) OS3D_CK(join_side(b, s));
     PassArgs zf = args_base(b);
     zf.in = w.A[0];
-    zf.in2 = q >= 2 ? w.A[1] : nullptr;
+    zf.in2 = (b->p.overlap && q >= 2) ? w.A[1] : nullptr;
     zf.out = w.T0;
     zf.mult = use_m ? b->GM : b->Gs;
     OS3D_CK(counted_launch(OS3D_KIND_Z_INV_FINAL, s,
@@ -837,12 +838,12 @@ os3d_status os3d_forward(const os3d_bank* b, const float* f, int batch, void* U,
     OS3D_CK(counted_launch(OS3D_KIND_Z_FWD_PREP, s,
                            [&] { return launch_z(nz, Z_FWD_PREP, 0, zp, tiles, s); }));
     // (a5) per block of orientation pairs, alternating between the side streams
-    OS3D_CK(fork_side(b, s));
+    if (b->p.overlap) OS3D_CK(fork_side(b, s));
     int q = 0;
     for (int s0 = 0; s0 < nslots; s0 += b->block_slots, ++q) {
       const int ns = std::min(b->block_slots, nslots - s0);
-      const int k = q & 1;
-      cudaStream_t st = b->side[k];
+      const int k = b->p.overlap ? (q & 1) : 0;
+      cudaStream_t st = b->p.overlap ? b->side[k] : s;
       PassArgs za = args_base(b);
       set_slots(b, za, v, s0, ns);
       za.in = w.fh;
@@ -855,7 +856,7 @@ os3d_status os3d_forward(const os3d_bank* b, const float* f, int batch, void* U,
       OS3D_CK(counted_launch(OS3D_KIND_XY_FWD_SCORE, st,
                              [&] { return launch_plane(b, XY_FWD_SCORE, udtype, xa, st); }));
     }
-    OS3D_CK(join_side(b, s));
+    if (b->p.overlap) OS3D_CK(join_side(b, s));
   }
   return OS3D_OK;
 }

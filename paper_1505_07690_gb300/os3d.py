@@ -24,7 +24,13 @@ _STATUS = {0: "OS3D_OK", 1: "OS3D_EINVAL", 2: "OS3D_ENOMEM", 3: "OS3D_ECUDA",
 class os3d_params(ctypes.Structure):
     _fields_ = [("k", ctypes.c_int), ("s_theta", ctypes.c_double), ("L", ctypes.c_int),
                 ("N", ctypes.c_int), ("gamma", ctypes.c_double), ("eps", ctypes.c_double),
-                ("fit_mode", ctypes.c_int), ("block_slots", ctypes.c_int)]
+                ("fit_mode", ctypes.c_int), ("block_slots", ctypes.c_int),
+                ("overlap", ctypes.c_int)]
+
+
+class os3d_server_config(ctypes.Structure):
+    _fields_ = [("arena_bytes", ctypes.c_size_t), ("max_inflight", ctypes.c_int),
+                ("udtype", ctypes.c_int)]
 
 
 class OS3DError(RuntimeError):
@@ -65,13 +71,22 @@ def lib():
         L.os3d_profile_read.argtypes = [i, ctypes.POINTER(ctypes.c_ulonglong), ctypes.POINTER(d)]
         L.os3d_profile_reset.argtypes = []
         L.os3d_forward_static.argtypes = [vp, vp, i, vp, i, vp]
+        L.os3d_server_default_config.argtypes = [ctypes.POINTER(os3d_server_config)]
+        L.os3d_server_create.argtypes = [ctypes.POINTER(os3d_server_config),
+                                         ctypes.POINTER(os3d_params), ctypes.POINTER(vp)]
+        L.os3d_server_submit.argtypes = [vp, ctypes.POINTER(i), i, vp, vp,
+                                         ctypes.POINTER(ctypes.c_longlong)]
+        L.os3d_server_wait.argtypes = [vp, ctypes.c_longlong, d, ctypes.POINTER(d)]
+        L.os3d_server_destroy.argtypes = [vp]
         L.os3d_kernel_kind_name.restype = ctypes.c_char_p
         L.os3d_kernel_kind_name.argtypes = [i]
         for name in ("os3d_default_params", "os3d_icosa_orientations", "os3d_make_wavelets",
                      "os3d_forward", "os3d_inverse", "os3d_adjoint", "os3d_bank_info",
                      "os3d_bank_coefficients", "os3d_bank_minv", "os3d_destroy_bank",
                      "os3d_profile_enable", "os3d_profile_read", "os3d_profile_reset",
-                     "os3d_forward_static"):
+                     "os3d_forward_static", "os3d_server_default_config",
+                     "os3d_server_create", "os3d_server_submit", "os3d_server_wait",
+                     "os3d_server_destroy"):
             getattr(L, name).restype = i
         _lib = L
     return _lib
@@ -288,3 +303,64 @@ def os3d_profile_read():
         _check(lib().os3d_profile_read(k, ctypes.byref(n), ctypes.byref(ms)), "os3d_profile_read")
         out[lib().os3d_kernel_kind_name(k).decode()] = (int(n.value), float(ms.value))
     return out
+
+
+# ---------------------------------------------------------------------------
+# serving
+# ---------------------------------------------------------------------------
+def os3d_server_default_config(**overrides) -> os3d_server_config:
+    c = os3d_server_config()
+    _check(lib().os3d_server_default_config(ctypes.byref(c)), "os3d_server_default_config")
+    for k, v in overrides.items():
+        setattr(c, k, v)
+    return c
+
+
+class Server:
+    """os3d_server: queued forward + inverse requests on one GPU. Host buffers
+    are page-locked torch tensors kept alive until each request is waited for."""
+
+    def __init__(self, config: os3d_server_config | None = None, params: os3d_params | None = None):
+        self.handle = None
+        cfg = config if config is not None else os3d_server_default_config()
+        h = ctypes.c_void_p(0)
+        _check(lib().os3d_server_create(ctypes.byref(cfg), None if params is None else ctypes.byref(params),
+                                        ctypes.byref(h)), "os3d_server_create")
+        self.handle = h
+        self._keep = {}
+
+    def submit(self, f_host, subdiv: int, f_out=None) -> int:
+        """Queue f_host (pinned float32 CPU tensor (nz, ny, nx)); returns the ticket."""
+        import torch
+        if f_host.device.type != "cpu" or f_host.dtype != torch.float32 or not f_host.is_contiguous():
+            raise ValueError("f_host must be a contiguous float32 CPU tensor")
+        if f_out is None:
+            f_out = torch.empty_like(f_host).pin_memory()
+        dims = (ctypes.c_int * 3)(*[int(x) for x in f_host.shape[-3:]])
+        t = ctypes.c_longlong(0)
+        _check(lib().os3d_server_submit(self.handle, dims, int(subdiv), _ptr(f_host), _ptr(f_out),
+                                        ctypes.byref(t)), "os3d_server_submit")
+        self._keep[t.value] = (f_host, f_out)
+        return t.value
+
+    def wait(self, ticket: int, timeout_s: float = 60.0):
+        """(f_out tensor, latency in ms); raises OS3DError (OS3D_ETIMEOUT on timeout)."""
+        lat = ctypes.c_double(0.0)
+        st = lib().os3d_server_wait(self.handle, ctypes.c_longlong(ticket), float(timeout_s),
+                                    ctypes.byref(lat))
+        if st == 4:
+            raise OS3DError(st, "os3d_server_wait")
+        f_host, f_out = self._keep.pop(ticket)
+        _check(st, "os3d_server_wait")
+        return f_out, lat.value
+
+    def close(self):
+        if self.handle:
+            _check(lib().os3d_server_destroy(self.handle), "os3d_server_destroy")
+            self.handle = None
+            self._keep.clear()
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.os3d_server_destroy(self.handle)
+            self.handle = None
