@@ -61,6 +61,8 @@ class Params:
     eps: float = 1e-4     # clamp M -> max(M, eps) of Sec. 3.1
     fit_mode: int = 1     # 1: paper's pseudo-inverse on tessellation order 15
                           # 0: L2 projection by Gauss-Legendre quadrature
+    profile: int = 0      # 0: cake wavelet h = F A + antisym(A) (line + edge detector)
+                          # 1: h = A (plate + edge detector, first construction of Sec. 3.1)
 
 
 # ---------------------------------------------------------------------------
@@ -230,6 +232,24 @@ def _canonical_order(V):
     return out
 
 
+def octahedron():
+    """6 unit vertices +-e_x, +-e_y, +-e_z and the 8 faces (one per octant)."""
+    V = np.array([[1.0, 0, 0], [-1.0, 0, 0], [0, 1.0, 0], [0, -1.0, 0], [0, 0, 1.0], [0, 0, -1.0]])
+    F = [(a, b, c) for a in (0, 1) for b in (2, 3) for c in (4, 5)]
+    return V, F
+
+
+def octa_orientations(subdiv):
+    """Octahedron subdivided ``subdiv`` times (the other platonic-solid sampling
+    of Sec. 2.1): 6, 18, 66, ... unit vectors, in canonical order. Unlike the
+    icosahedral sets it is mapped onto itself by the 90-degree rotations
+    about the coordinate axes."""
+    V, F = octahedron()
+    for _ in range(subdiv):
+        V, F = subdivide(V, F)
+    return _canonical_order(np.asarray(V))
+
+
 def icosa_orientations(subdiv):
     """Icosahedron subdivided ``subdiv`` times: 12, 42, 162, ... unit vectors,
     both members of every antipodal pair kept, in canonical order."""
@@ -318,9 +338,14 @@ def normalise(c, n_o):
 
 
 def wavelet_coefficients(p: Params, n_o):
-    """Normalised Legendre coefficients c of the cake-wavelet angular part
-    h = h_Re + h_Im (Sec. 3.1, Eq. CakeWaveletRe and Eq. Antisymmetrize)."""
-    ce, co = funk_antisym(fit_coefficients(p))
+    """Normalised Legendre coefficients c of the angular part: for the cake
+    wavelet h = h_Re + h_Im (Sec. 3.1, Eq. CakeWaveletRe and
+    Eq. Antisymmetrize); for the plate detector h = A itself (Sec. 3.1,
+    the construction before Eq. Antisymmetrize, Fig. 3)."""
+    b = fit_coefficients(p)
+    if p.profile == 1:
+        return normalise(b, n_o)
+    ce, co = funk_antisym(b)
     return normalise(ce + co, n_o)
 
 
@@ -425,3 +450,48 @@ def orientation_pairs(orients, tol=1e-9):
         if len(j):
             out[i] = int(j[0])
     return out
+
+
+# ---------------------------------------------------------------------------
+# Approximate reconstruction and projection (Sec. 2.1, Eq.
+# Reconstruction2Approximation; App. A, corollary on P_psi)
+# ---------------------------------------------------------------------------
+def approx_weight(bank: Bank):
+    """Discrete weight of the orientation integral in Eq.
+    Reconstruction2Approximation: the paper's condition that the orientation
+    integral of the wavelets' Fourier transforms be ~1 is met exactly at w = 0,
+    where every psi_hat_i equals c_0, so d sigma -> 1 / (N_o c_0)."""
+    return 1.0 / (bank.n_o * bank.c[0])
+
+
+def approx_reconstruct(U, bank: Bank):
+    """f ~ Re sum_i U_i d sigma (Eq. Reconstruction2Approximation)."""
+    acc = np.zeros(bank.dims, dtype=np.float64)
+    for i in range(bank.n_o):
+        acc += np.real(U[i])
+    return approx_weight(bank) * acc
+
+
+def project(U, bank: Bank):
+    """P_psi U = W W^{*,ext} U: the exact reconstruction (the adjoint extended
+    to the embedding space with the M_psi inner product) followed by the
+    forward transform (App. A, corollary)."""
+    return forward(inverse(U, bank), bank)
+
+
+# ---------------------------------------------------------------------------
+# Score-domain processing Upsilon = W^{*,ext} o Phi o W (Sec. 4.1)
+# ---------------------------------------------------------------------------
+def soft_threshold(U, power=1.5):
+    """Phi(U) = |U|^p sgn(U) (Sec. 4.1, Fig. 6), applied to the real part
+    (line response) and the imaginary part (edge response) separately."""
+    U = np.asarray(U)
+    re = np.sign(U.real) * np.abs(U.real) ** power
+    im = np.sign(U.imag) * np.abs(U.imag) ** power
+    return re + 1j * im
+
+
+def upsilon(f, bank: Bank, power=1.5):
+    """Upsilon f = W^{*,ext} Phi W f = W^* P_psi Phi W f (Sec. 4.1), with the
+    soft threshold Phi and the exact (clamped) reconstruction as W^{*,ext}."""
+    return inverse(soft_threshold(forward(f, bank), power), bank)

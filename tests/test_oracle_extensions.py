@@ -1,0 +1,178 @@
+"""Pins of the oracle's extensions: the octahedral orientation sets, the plate
+detector profile, the approximate reconstruction, the projection P_psi and
+the soft-threshold processing Upsilon. As in test_oracle_pins.py, each test
+checks the oracle against something other than itself: a spherical design
+identity, grid rotations, the detector semantics the paper states, and
+algebraic properties (fixed points, idempotence, homogeneity)."""
+import numpy as np
+import pytest
+
+from oracle import os3d_oracle as O
+
+pytestmark = pytest.mark.filterwarnings("ignore::DeprecationWarning")
+
+
+# ---------------------------------------------------------------------------
+# octahedral orientation sets (Sec. 2.1: platonic solids and tessellations)
+# ---------------------------------------------------------------------------
+def _rot_z90():
+    return np.array([[0.0, -1.0, 0.0], [1.0, 0.0, 0.0], [0.0, 0.0, 1.0]])
+
+
+def _rot_x90():
+    return np.array([[1.0, 0.0, 0.0], [0.0, 0.0, -1.0], [0.0, 1.0, 0.0]])
+
+
+def _act(R, f):
+    """g(r) = f(R^T r) on a periodic cubic grid, array axes (z, y, x)."""
+    n = f.shape[0]
+    r = np.stack(np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij"), -1)
+    xyz = r[..., ::-1]                                  # (x, y, z) of every voxel
+    src = np.einsum("ji,abcj->abci", R, xyz).round().astype(int) % n   # R^T r
+    return f[src[..., 2], src[..., 1], src[..., 0]]
+
+
+@pytest.mark.parametrize("subdiv,count", [(0, 6), (1, 18), (2, 66), (3, 258)])
+def test_octahedral_sets(subdiv, count):
+    V = O.octa_orientations(subdiv)
+    assert V.shape == (count, 3)
+    assert np.allclose(np.linalg.norm(V, axis=1), 1.0, atol=1e-15)
+    h = count // 2
+    assert np.allclose(V[h:], -V[:h], atol=0)
+    # closed under the 90-degree rotations about the axes (as sets)
+    for R in (_rot_z90(), _rot_x90()):
+        RV = V @ R.T
+        d = np.abs(RV[:, None, :] - V[None, :, :]).max(-1)
+        assert np.all(d.min(1) < 1e-12)
+        assert len(set(np.argmin(d, 1))) == count
+
+
+def test_channel_permutation_under_90_degree_rotations():
+    """W[f o R^-1](x, R n) = W[f](R^-1 x, n): rotating the image by 90 degrees
+    about an axis permutes the channels of the octahedral set and rotates
+    each channel (exact on a cubic periodic grid with the ball limit)."""
+    n = 12
+    dims = (n, n, n)
+    f = np.random.default_rng(31).standard_normal(dims)
+    bank = O.Bank(dims, O.octa_orientations(1), O.Params(L=12))
+    U = O.forward(f, bank)
+    V = bank.orients
+    for R in (_rot_z90(), _rot_x90()):
+        g = _act(R, f)
+        r = np.array([3, 1, 2])
+        src = (R.T @ r).round().astype(int) % n
+        assert g[r[2], r[1], r[0]] == f[src[2], src[1], src[0]]
+        perm = [int(np.argmin(np.abs(V - rv).sum(1))) for rv in V @ R.T]
+        U2 = O.forward(g, bank)
+        for i in range(bank.n_o):
+            assert np.allclose(U2[perm[i]], _act(R, U[i]), atol=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# plate detector h = A versus the cake wavelet (Sec. 3.1, Fig. 3 and Fig. 4)
+# ---------------------------------------------------------------------------
+def _center_real_responses(f, bank):
+    U = O.forward(f, bank)
+    c = tuple(d // 2 for d in f.shape)
+    return np.array([U[i][c].real for i in range(bank.n_o)])
+
+
+def test_plate_and_line_detectors():
+    """With h = A the real part detects plates perpendicular to n; after the
+    Funk transform it detects lines along n."""
+    n = 24
+    dims = (n, n, n)
+    z, y, x = np.meshgrid(*(np.arange(n) - n // 2,) * 3, indexing="ij")
+    line_z = np.exp(-(x ** 2 + y ** 2) / (2 * 1.5 ** 2))
+    plate_z = np.exp(-(z ** 2) / (2 * 1.5 ** 2))
+    V = O.octa_orientations(1)
+    ez = {0, len(V) // 2}                 # +e_z and -e_z in canonical order
+    assert np.allclose(V[0], [0, 0, 1])
+    cake = O.Bank(dims, V, O.Params(L=16, profile=0))
+    plate = O.Bank(dims, V, O.Params(L=16, profile=1))
+    assert int(np.argmax(_center_real_responses(line_z, cake))) in ez
+    assert int(np.argmax(_center_real_responses(plate_z, plate))) in ez
+    assert int(np.argmax(_center_real_responses(plate_z, cake))) not in ez
+    assert int(np.argmax(_center_real_responses(line_z, plate))) not in ez
+
+
+def test_plate_profile_coefficients_are_the_normalised_fit():
+    p = O.Params(L=12, profile=1, fit_mode=0)
+    b = O.fit_coefficients(p)
+    c = O.wavelet_coefficients(p, 42)
+    ratio = c / b
+    assert np.allclose(ratio, ratio[0], rtol=1e-13)
+    l = np.arange(13)
+    assert abs(42 * np.sum(c * c / (2 * l + 1)) - 1.0) < 1e-13
+
+
+# ---------------------------------------------------------------------------
+# approximate reconstruction (Eq. Reconstruction2Approximation)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("L,exact", [(4, True), (5, True), (6, False)])
+def test_approximate_reconstruction_on_a_spherical_5_design(L, exact):
+    """The 12 icosahedron vertices form a spherical 5-design, so for L <= 5
+    sum_i h(w.n_i) = N_o c_0 for every direction and the approximate
+    reconstruction equals IDFT[ f_hat g 1_ball ] exactly; at L = 6 it does not."""
+    dims = (10, 12, 8)
+    f = np.random.default_rng(32).standard_normal(dims)
+    bank = O.Bank(dims, O.icosa_orientations(0), O.Params(L=L, fit_mode=0))
+    U = O.forward(f, bank)
+    fa = O.approx_reconstruct(U, bank)
+    ref = np.fft.ifftn(np.fft.fftn(f) * O.radial_ball(dims, 8, 0.8)).real
+    err = np.abs(fa - ref).max() / np.abs(ref).max()
+    assert (err < 1e-13) == exact
+    # the odd (edge) parts cancel over antipodal pairs: the sum is real
+    assert np.abs(U.sum(0).imag).max() < 1e-13 * np.abs(U).max()
+
+
+def test_approximate_reconstruction_keeps_the_mean():
+    dims = (8, 8, 8)
+    bank = O.Bank(dims, O.icosa_orientations(1), O.Params(L=16))
+    f = np.full(dims, 3.25)
+    assert np.allclose(O.approx_reconstruct(O.forward(f, bank), bank), 3.25, atol=1e-13)
+
+
+# ---------------------------------------------------------------------------
+# projection P_psi = W W^{*,ext} (App. A, corollary)
+# ---------------------------------------------------------------------------
+def test_projection_fixes_scores_and_is_idempotent():
+    dims = (10, 12, 8)
+    rng = np.random.default_rng(33)
+    bank = O.Bank(dims, O.icosa_orientations(1), O.Params(L=8))
+    f = rng.standard_normal(dims)
+    U = O.forward(f, bank)
+    assert np.abs(O.project(U, bank) - U).max() < 1e-13 * np.abs(U).max()
+    G = rng.standard_normal(U.shape) + 1j * rng.standard_normal(U.shape)
+    P1 = O.project(G, bank)
+    assert np.abs(O.project(P1, bank) - P1).max() < 1e-13 * np.abs(P1).max()
+    # the projection of anything is the score of a real image: antipodes conjugate
+    h = bank.n_o // 2
+    assert np.abs(P1[h:] - np.conj(P1[:h])).max() < 1e-13 * np.abs(P1).max()
+    assert np.abs(P1 - G).max() > 0.1 * np.abs(G).max()
+
+
+# ---------------------------------------------------------------------------
+# soft thresholding and Upsilon (Sec. 4.1, Fig. 6)
+# ---------------------------------------------------------------------------
+def test_soft_threshold_values():
+    U = np.array([-2.0 + 3.0j, 0.5 - 0.25j, 0.0 + 0.0j])
+    assert np.allclose(O.soft_threshold(U, 2.0), [-4.0 + 9.0j, 0.25 - 0.0625j, 0.0])
+    assert np.allclose(O.soft_threshold(U, 1.5),
+                       [-2.0 ** 1.5 + 3.0 ** 1.5 * 1j, 0.5 ** 1.5 - 0.25 ** 1.5 * 1j, 0.0])
+    assert np.array_equal(O.soft_threshold(U, 1.0), U)
+
+
+def test_upsilon_identities():
+    dims = (8, 10, 12)
+    rng = np.random.default_rng(34)
+    bank = O.Bank(dims, O.icosa_orientations(1), O.Params(L=8))
+    f = rng.standard_normal(dims)
+    # p = 1: Phi is the identity and Upsilon the ball projection
+    ref = np.fft.ifftn(np.fft.fftn(f) * (bank.G > 0)).real
+    assert np.abs(O.upsilon(f, bank, 1.0) - ref).max() < 1e-12
+    u = O.upsilon(f, bank, 1.5)
+    # odd and positively homogeneous of degree p
+    assert np.abs(O.upsilon(-f, bank, 1.5) + u).max() < 1e-12 * np.abs(u).max()
+    assert np.abs(O.upsilon(4.0 * f, bank, 1.5) - 8.0 * u).max() < 1e-12 * np.abs(u).max()
+    assert np.abs(u - ref).max() > 0.01 * np.abs(ref).max()
