@@ -337,6 +337,35 @@ def run_ours(args):
                    "share": v[1] / max(sum(x[1] for x in prof.values()), 1e-9)}
                for k, v in prof.items() if v[0]}
 
+    # ---- the score-domain operations on the same workload (CUDA events)
+    def timed(fn, n):
+        fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(n):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / n
+
+    hbm = peaks["hbm_gbs"]
+    ops = {}
+    ms_a = timed(lambda: os3d.os3d_approx_reconstruct(bank, U, frec), args.steps)
+    by_a = n_o * nvox * esize + nvox * 4
+    ops["approx_reconstruct"] = {"ms": ms_a, "bytes": by_a, "achieved_gbs": by_a / ms_a / 1e6,
+                                 "frac_hbm": by_a / ms_a / 1e6 / hbm}
+    ms_p = timed(lambda: os3d.os3d_project(bank, U, U), args.steps)
+    ops["project"] = {"ms": ms_p, "value": nvox * n_o / (ms_p / 1e3), "unit": UNIT}
+    ms_s = timed(lambda: os3d.os3d_soft_threshold(U, 1.5, out=U), args.steps)
+    by_s = 2 * n_o * nvox * esize
+    ops["soft_threshold"] = {"ms": ms_s, "bytes": by_s, "achieved_gbs": by_s / ms_s / 1e6,
+                             "frac_hbm": by_s / ms_s / 1e6 / hbm}
+    fu = torch.empty_like(f)
+    ms_u = timed(lambda: os3d.os3d_upsilon(bank, f, 1.5, fu), args.steps)
+    ops["upsilon_fused"] = {"ms": ms_u, "value": nvox * n_o / (ms_u / 1e3), "unit": UNIT,
+                            "score_bytes_stored": 0}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, dt, desc = oracle_sample_rate(8)
@@ -357,6 +386,7 @@ def run_ours(args):
             "roofline": roof,
             "step_hbm": {"bytes": step_bytes, "achieved_gbs": step_bytes / (total_ms / args.steps / 1e3) / 1e9},
             "kernels": kernels,
+            "ops": ops,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": nvox * 4,
                     "d2h_bytes_per_step": nvox * 4},

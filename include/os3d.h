@@ -76,12 +76,15 @@ typedef struct {
   int overlap;      /* 1: consecutive blocks alternate between two internal streams of the
                        bank (forked from and joined to the caller's stream); 0: every launch
                        on the caller's stream (for callers running many transforms at once) */
+  int profile;      /* angular part h: 0 = cake wavelet, h = F A + antisym(A) (line and edge
+                       detector, Sec. 3.1, Eq. CakeWaveletRe / Eq. Antisymmetrize);
+                       1 = h = A itself (plate and edge detector, Sec. 3.1, Fig. 3)   */
 } os3d_params;
 
 typedef struct os3d_bank os3d_bank; /* opaque, library-owned */
 
 /* Defaults: k = 2, s_theta = 0.7, L = 16, N = 8, gamma = 0.8, eps = 1e-4,
- * fit_mode = 1, block_slots = 0, overlap = 1. Host only. */
+ * fit_mode = 1, block_slots = 0, overlap = 1, profile = 0. Host only. */
 os3d_status os3d_default_params(os3d_params* p);
 
 /* Orientation set of Sec. 2.1: an icosahedron (vertices: cyclic permutations
@@ -96,12 +99,20 @@ os3d_status os3d_default_params(os3d_params* p);
  * (then *n_o still receives the required count). */
 os3d_status os3d_icosa_orientations(int subdiv, double* out, int capacity, int* n_o);
 
+/* The other platonic-solid sampling of Sec. 2.1: an octahedron (vertices
+ * +-e_x, +-e_y, +-e_z) subdivided `subdiv` times in the same way: 6, 18, 66,
+ * 258, 1026, 4098 unit vectors, in the same canonical order. It is mapped onto
+ * itself by the 90-degree rotations about the coordinate axes, which on a
+ * cubic grid permute the channels of a score exactly. Host only; subdiv 0..5;
+ * errors as os3d_icosa_orientations. */
+os3d_status os3d_octa_orientations(int subdiv, double* out, int capacity, int* n_o);
+
 /* Builds the wavelet bank for a grid dims = {nz, ny, nx} and the orientation
  * set `orient` (host, n_o x 3 doubles, unit vectors, x y z). Steps (all on
  * the device current at the call, stream-ordered on `stream`):
  *  (a1) zonal fit b_l of A (FP64 kernel), Funk transform c^e_l = 2 pi P_l(0) b_l,
  *       anti-symmetrisation c^o_l = (1 - (-1)^l) b_l, c = kappa (c^e + c^o)
- *       (Sec. 3.2);
+ *       (Sec. 3.2); with profile = 1, c = kappa b;
  *  (a3) M = G^2 sum_i h(w_hat . n_i)^2 in FP64 and the factors
  *       G / n^3 and G / (n^3 max(M, eps)) stored as float (Sec. 2.1, 3.1).
  * Antipodal pairs in `orient` are detected (|n_i + n_j| < 1e-9) and share
@@ -134,6 +145,45 @@ os3d_status os3d_inverse(const os3d_bank* bank, const void* U, os3d_udtype udtyp
  * in PyTorch's convention this is dL/df. Errors: EINVAL, ECUDA. */
 os3d_status os3d_adjoint(const os3d_bank* bank, const void* G, os3d_udtype udtype, int batch,
                          float* grad_f, void* workspace, void* stream);
+
+/* Approximate reconstruction (Eq. Reconstruction2Approximation):
+ * f_out = w Re sum_i U_i with the discrete measure w = 1 / (N_o c_0), the
+ * value that makes the orientation sum of the wavelets exactly 1 at w = 0
+ * (where every psi_hat_i equals c_0), i.e. the paper's condition
+ * (2 pi)^(3/2) int F[psi_n] d sigma ~ 1 read at the origin. No Fourier
+ * transform: one streaming pass over U (device, batch scores) into f_out
+ * (device, batch x nz x ny x nx float, 16-byte aligned). Errors: EINVAL
+ * (also when c_0 = 0), ECUDA. */
+os3d_status os3d_approx_reconstruct(const os3d_bank* bank, const void* U, os3d_udtype udtype,
+                                    int batch, float* f_out, void* stream);
+
+/* Projection onto the space of orientation scores (App. A, corollary):
+ * P_psi U = W W^{*,ext} U, with W^{*,ext} the exact reconstruction (the
+ * adjoint extended to the embedding space with the M_psi inner product), i.e.
+ * os3d_inverse followed by os3d_forward, per volume. U and U_out (device,
+ * batch scores of udtype) may be the same buffer. The intermediate image is
+ * kept in the workspace. Errors: EINVAL, ECUDA. */
+os3d_status os3d_project(const os3d_bank* bank, const void* U, os3d_udtype udtype, int batch,
+                         void* U_out, void* workspace, void* stream);
+
+/* Soft thresholding Phi(U) = |U|^p sgn(U) of Sec. 4.1 (Fig. 6 uses p = 1.5),
+ * applied to the real (line) and imaginary (edge) parts separately, on
+ * `count` complex elements (a multiple of 4) of `in` into `out` (device,
+ * 16-byte aligned, may be equal). BF16 results round to nearest even.
+ * Errors: EINVAL (count, alignment, p <= 0 or not finite), ECUDA. */
+os3d_status os3d_soft_threshold(const void* in, void* out, os3d_udtype udtype, long long count,
+                                double power, void* stream);
+
+/* Score-domain processing with soft thresholding (Sec. 4.1):
+ * Upsilon f = W^{*,ext} Phi W f = W^* P_psi Phi W f, the exact (clamped)
+ * reconstruction of the soft-thresholded score, for `batch` real volumes f
+ * into f_out (device, float). Equal to os3d_forward, os3d_soft_threshold and
+ * os3d_inverse in sequence (complex64 scores), but the score is never
+ * stored: per block of orientation pairs the thresholding runs between the
+ * inverse and the forward 2D DFT of each plane in one kernel, so the call
+ * needs only the bank's workspace. Errors: EINVAL, ECUDA. */
+os3d_status os3d_upsilon(const os3d_bank* bank, const float* f, int batch, float* f_out,
+                         double power, void* workspace, void* stream);
 
 /* Sizes: workspace bytes one call needs, and device bytes of one volume's
  * score (N_o x nz x ny x nx x 8). Host only. */
@@ -229,7 +279,10 @@ enum {
   OS3D_KIND_Z_FWD_SCORE = 5,   /* forward: wavelet evaluation and IDFT_z       */
   OS3D_KIND_Z_INV_SCORE = 6,   /* inverse: DFT_z, wavelet and orientation sum  */
   OS3D_KIND_Z_INV_FINAL = 7,   /* inverse: factor G / (n^3 max(M,eps)), IDFT_z */
-  OS3D_KIND_COUNT = 8
+  OS3D_KIND_XY_SOFT = 8,       /* Upsilon: IDFT_xy, soft threshold, DFT_xy     */
+  OS3D_KIND_APPROX = 9,        /* approximate reconstruction: orientation sum  */
+  OS3D_KIND_SOFT = 10,         /* soft threshold of a stored score             */
+  OS3D_KIND_COUNT = 11
 };
 
 /* Number of kernels this library has launched in this process. Host only. */

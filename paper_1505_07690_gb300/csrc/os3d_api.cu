@@ -147,6 +147,15 @@ void icosahedron(std::vector<V3>& V, std::vector<std::array<int, 3>>& F) {
         if (adj(i, j) && adj(j, k) && adj(i, k)) F.push_back({i, j, k});
 }
 
+void octahedron(std::vector<V3>& V, std::vector<std::array<int, 3>>& F) {
+  V = {{1.0, 0.0, 0.0}, {-1.0, 0.0, 0.0}, {0.0, 1.0, 0.0},
+       {0.0, -1.0, 0.0}, {0.0, 0.0, 1.0}, {0.0, 0.0, -1.0}};
+  F.clear();
+  for (int a = 0; a < 2; ++a)
+    for (int b = 2; b < 4; ++b)
+      for (int c = 4; c < 6; ++c) F.push_back({a, b, c});   // one face per octant
+}
+
 void subdivide(std::vector<V3>& V, std::vector<std::array<int, 3>>& F) {
   std::map<std::pair<int, int>, int> mid;
   auto m = [&](int a, int b) {
@@ -311,7 +320,8 @@ bool axis_ok(int n) { return z_supported(n); }
 os3d_status check_params(const os3d_params& p) {
   if (p.k < 0 || p.k > 8 || !(p.s_theta > 0.0) || p.L < 0 || p.L > kMaxL || p.N < 0 || p.N > 64 ||
       !(p.gamma > 0.0 && p.gamma < 1.0) || !(p.eps > 0.0) || (p.fit_mode != 0 && p.fit_mode != 1) ||
-      p.block_slots < 0 || p.block_slots > kMaxSlots || (p.overlap != 0 && p.overlap != 1))
+      p.block_slots < 0 || p.block_slots > kMaxSlots || (p.overlap != 0 && p.overlap != 1) ||
+      (p.profile != 0 && p.profile != 1))
     return OS3D_EINVAL;
   return OS3D_OK;
 }
@@ -407,6 +417,7 @@ os3d_status os3d_default_params(os3d_params* p) {
   p->fit_mode = 1;
   p->block_slots = 0;
   p->overlap = 1;
+  p->profile = 0;
   return OS3D_OK;
 }
 
@@ -418,6 +429,22 @@ os3d_status os3d_icosa_orientations(int subdiv, double* out, int capacity, int* 
   std::vector<V3> V;
   std::vector<std::array<int, 3>> F;
   icosahedron(V, F);
+  for (int s = 0; s < subdiv; ++s) subdivide(V, F);
+  std::vector<V3> o;
+  if ((int)V.size() != n || !canonical_order(V, o)) return OS3D_EINVAL;
+  for (int i = 0; i < n; ++i)
+    for (int q = 0; q < 3; ++q) out[3 * i + q] = o[i][q];
+  return OS3D_OK;
+}
+
+os3d_status os3d_octa_orientations(int subdiv, double* out, int capacity, int* n_o) {
+  if (subdiv < 0 || subdiv > 5 || !n_o) return OS3D_EINVAL;
+  const int n = 4 * (1 << (2 * subdiv)) + 2;
+  *n_o = n;
+  if (!out || capacity < n) return OS3D_EINVAL;
+  std::vector<V3> V;
+  std::vector<std::array<int, 3>> F;
+  octahedron(V, F);
   for (int s = 0; s < subdiv; ++s) subdivide(V, F);
   std::vector<V3> o;
   if ((int)V.size() != n || !canonical_order(V, o)) return OS3D_EINVAL;
@@ -552,7 +579,7 @@ os3d_status os3d_make_wavelets(const int dims[3], const double* orient, int n_o,
       cudaMemcpyAsync(dwt.p, wt.data(), sizeof(double) * wt.size(), cudaMemcpyHostToDevice, s))
     return fail(OS3D_ECUDA);
   if (launch_fit((const double*)dzt.p, (const double*)dwt.p, npts, p.fit_mode, p.k, p.s_theta, L,
-                 n_o, (double*)dout.p, s) != cudaSuccess)
+                 n_o, p.profile, (double*)dout.p, s) != cudaSuccess)
     return fail(OS3D_ECUDA);
   std::vector<double> bc(2 * (L + 1));
   if (cudaMemcpyAsync(bc.data(), dout.p, sizeof(double) * bc.size(), cudaMemcpyDeviceToHost, s) ||
@@ -735,29 +762,97 @@ cudaError_t launch_plane(const os3d_bank* b, int mode, int ub, const PassArgs& a
   cudaError_t e;
   switch (mode) {
     case XY_FWD_REAL:   // f -> DFT_x -> out, then DFT_y in place
+      g_launches.fetch_add(1);   // counted_launch counts one of the two
       e = launch_pencil(nx, PN_R2C, -1, 0, a, gx, lx, 1, s);
       if (e != cudaSuccess) return e;
       c.in = a.out;
       c.in_off = a.out_off;
       return launch_pencil(ny, PN_C2C, -1, 0, c, gy, ly, 1, s);
     case XY_INV_REAL:   // IDFT_y in place on in, then IDFT_x -> real out
+      g_launches.fetch_add(1);
       c.out = const_cast<void*>(a.in);
       c.out_off = a.in_off;
       e = launch_pencil(ny, PN_C2C, 1, 0, c, gy, ly, 1, s);
       if (e != cudaSuccess) return e;
       return launch_pencil(nx, PN_C2R, 1, 0, a, gx, lx, 1, s);
     case XY_FWD_SCORE:  // IDFT_y in place on T_s, then IDFT_x -> U_a, U_b
+      g_launches.fetch_add(1);
       c.out = const_cast<void*>(a.in);
       e = launch_pencil(ny, PN_C2C, 1, 0, c, gy, ly, ns, s);
       if (e != cudaSuccess) return e;
       return launch_pencil(nx, PN_C2U, 1, ub, a, gx, lx, ns, s);
     case XY_INV_SCORE:  // U_a + conj U_b -> DFT_x -> T_s, then DFT_y in place
+      g_launches.fetch_add(1);
       e = launch_pencil(nx, PN_U2C, -1, ub, a, gx, lx, ns, s);
       if (e != cudaSuccess) return e;
       c.in = a.out;
       return launch_pencil(ny, PN_C2C, -1, 0, c, gy, ly, ns, s);
     default: return cudaErrorInvalidValue;
   }
+}
+
+// The score-domain step of Upsilon on a block of intermediates T_s (in
+// place): the fused plane kernel, or for other planes the pencil passes
+// IDFT_y, IDFT_x, the soft threshold, DFT_x, DFT_y.
+cudaError_t launch_plane_soft(const os3d_bank* b, const PassArgs& a, cudaStream_t s) {
+  const int nz = b->dims[0], ny = b->dims[1], nx = b->dims[2];
+  if (xy_supported(ny, nx)) return launch_xy(ny, nx, XY_SOFT, 0, a, s);
+  const long long P = (long long)ny * nx;
+  const PencilGeom gx{ny, P, nx, 1};
+  const PencilGeom gy{nx, P, 1, nx};
+  const long long lx = (long long)nz * ny, ly = (long long)nz * nx;
+  PassArgs c = a;
+  c.in = a.out;
+  c.in_off = c.out_off = 0;
+  g_launches.fetch_add(4);   // five launches, one counted by counted_launch
+  cudaError_t e = launch_pencil(ny, PN_C2C, 1, 0, c, gy, ly, a.nslots, s);
+  if (e == cudaSuccess) e = launch_pencil(nx, PN_C2C, 1, 0, c, gx, lx, a.nslots, s);
+  if (e == cudaSuccess) e = launch_soft_slots(c, b->nvox, s);
+  if (e == cudaSuccess) e = launch_pencil(nx, PN_C2C, -1, 0, c, gx, lx, a.nslots, s);
+  if (e == cudaSuccess) e = launch_pencil(ny, PN_C2C, -1, 0, c, gy, ly, a.nslots, s);
+  return e;
+}
+
+size_t u_elem_bytes(int udtype) { return udtype == OS3D_U_BF16X2 ? 4 : 8; }
+
+// f_hat G / n^3 of volume v of f into w.fh (a4)
+os3d_status prep_fhat(const os3d_bank* b, const float* f, int v, const Work& w, cudaStream_t s) {
+  const int nz = b->dims[0], ny = b->dims[1], nx = b->dims[2];
+  const int tiles = ny * (nx / kTileX);
+  PassArgs x0 = args_base(b);
+  x0.in = f;
+  x0.in_off = (long long)v * b->nvox;
+  x0.out = w.T0;
+  OS3D_CK(counted_launch(OS3D_KIND_XY_FWD_REAL, s,
+                         [&] { return launch_plane(b, XY_FWD_REAL, 0, x0, s); }));
+  PassArgs zp = args_base(b);
+  zp.in = w.T0;
+  zp.out = w.fh;
+  zp.mult = b->Gs;
+  OS3D_CK(counted_launch(OS3D_KIND_Z_FWD_PREP, s,
+                         [&] { return launch_z(nz, Z_FWD_PREP, 0, zp, tiles, s); }));
+  return OS3D_OK;
+}
+
+// f = Re IDFT[ (A_0 + A_1) x mult ] of volume v into fout (end of a6 / a7)
+os3d_status finish_real(const os3d_bank* b, const Work& w, int nblocks, const float* mult,
+                        float* fout, int v, cudaStream_t s) {
+  const int nz = b->dims[0], ny = b->dims[1], nx = b->dims[2];
+  const int tiles = ny * (nx / kTileX);
+  PassArgs zf = args_base(b);
+  zf.in = w.A[0];
+  zf.in2 = (b->p.overlap && nblocks >= 2) ? w.A[1] : nullptr;
+  zf.out = w.T0;
+  zf.mult = mult;
+  OS3D_CK(counted_launch(OS3D_KIND_Z_INV_FINAL, s,
+                         [&] { return launch_z(nz, Z_INV_FINAL, 0, zf, tiles, s); }));
+  PassArgs xf = args_base(b);
+  xf.in = w.T0;
+  xf.out = fout;
+  xf.out_off = (long long)v * b->nvox;
+  OS3D_CK(counted_launch(OS3D_KIND_XY_INV_REAL, s,
+                         [&] { return launch_plane(b, XY_INV_REAL, 0, xf, s); }));
+  return OS3D_OK;
 }
 
 // inverse (use_m = true) or adjoint (use_m = false). Consecutive blocks of
@@ -792,32 +887,14 @@ os3d_status backward_impl(const os3d_bank* b, const void* U, int udtype, int bat
                              [&] { return launch_z(nz, Z_INV_SCORE, b->ev, za, tiles, st); }));
     }
     if (b->p.overlap) OS3D_CK(join_side(b, s));
-    PassArgs zf = args_base(b);
-    zf.in = w.A[0];
-    zf.in2 = (b->p.overlap && q >= 2) ? w.A[1] : nullptr;
-    zf.out = w.T0;
-    zf.mult = use_m ? b->GM : b->Gs;
-    OS3D_CK(counted_launch(OS3D_KIND_Z_INV_FINAL, s,
-                           [&] { return launch_z(nz, Z_INV_FINAL, 0, zf, tiles, s); }));
-    PassArgs xf = args_base(b);
-    xf.in = w.T0;
-    xf.out = fout;
-    xf.out_off = (long long)v * n;
-    OS3D_CK(counted_launch(OS3D_KIND_XY_INV_REAL, s,
-                           [&] { return launch_plane(b, XY_INV_REAL, 0, xf, s); }));
+    const os3d_status st = finish_real(b, w, q, use_m ? b->GM : b->Gs, fout, v, s);
+    if (st != OS3D_OK) return st;
   }
   return OS3D_OK;
 }
 
-}  // namespace
-
-extern "C" {
-
-os3d_status os3d_forward(const os3d_bank* b, const float* f, int batch, void* U,
-                         os3d_udtype udtype, void* ws, void* stream) {
-  const os3d_status st = check_call(b, f, U, batch, udtype, ws);
-  if (st != OS3D_OK) return st;
-  cudaStream_t s = (cudaStream_t)stream;
+os3d_status forward_impl(const os3d_bank* b, const float* f, int batch, void* U, int udtype,
+                         void* ws, cudaStream_t s) {
   const Work w = carve(b, ws);
   const int nz = b->dims[0], ny = b->dims[1], nx = b->dims[2];
   const int nslots = (int)b->slot_a.size();
@@ -825,18 +902,8 @@ os3d_status os3d_forward(const os3d_bank* b, const float* f, int batch, void* U,
   const long long n = b->nvox;
   for (int v = 0; v < batch; ++v) {
     // (a4) f_hat G / n^3
-    PassArgs x0 = args_base(b);
-    x0.in = f;
-    x0.in_off = (long long)v * n;
-    x0.out = w.T0;
-    OS3D_CK(counted_launch(OS3D_KIND_XY_FWD_REAL, s,
-                           [&] { return launch_plane(b, XY_FWD_REAL, 0, x0, s); }));
-    PassArgs zp = args_base(b);
-    zp.in = w.T0;
-    zp.out = w.fh;
-    zp.mult = b->Gs;
-    OS3D_CK(counted_launch(OS3D_KIND_Z_FWD_PREP, s,
-                           [&] { return launch_z(nz, Z_FWD_PREP, 0, zp, tiles, s); }));
+    const os3d_status st = prep_fhat(b, f, v, w, s);
+    if (st != OS3D_OK) return st;
     // (a5) per block of orientation pairs, alternating between the side streams
     if (b->p.overlap) OS3D_CK(fork_side(b, s));
     int q = 0;
@@ -861,6 +928,61 @@ os3d_status os3d_forward(const os3d_bank* b, const float* f, int batch, void* U,
   return OS3D_OK;
 }
 
+// Upsilon f = W^{*,ext} Phi W f (Sec. 4.1): per block, the z-pass of the
+// forward transform, the fused score-domain step and the z-pass of the
+// inverse; the score itself is never stored.
+os3d_status upsilon_impl(const os3d_bank* b, const float* f, int batch, float* fout, float power,
+                         void* ws, cudaStream_t s) {
+  const Work w = carve(b, ws);
+  const int nz = b->dims[0], ny = b->dims[1], nx = b->dims[2];
+  const int nslots = (int)b->slot_a.size();
+  const int tiles = ny * (nx / kTileX);
+  for (int v = 0; v < batch; ++v) {
+    const os3d_status st = prep_fhat(b, f, v, w, s);
+    if (st != OS3D_OK) return st;
+    if (b->p.overlap) OS3D_CK(fork_side(b, s));
+    int q = 0;
+    for (int s0 = 0; s0 < nslots; s0 += b->block_slots, ++q) {
+      const int ns = std::min(b->block_slots, nslots - s0);
+      const int k = b->p.overlap ? (q & 1) : 0;
+      cudaStream_t st2 = b->p.overlap ? b->side[k] : s;
+      PassArgs za = args_base(b);
+      set_slots(b, za, v, s0, ns);
+      za.in = w.fh;
+      za.out = w.T[k];
+      OS3D_CK(counted_launch(OS3D_KIND_Z_FWD_SCORE, st2,
+                             [&] { return launch_z(nz, Z_FWD_SCORE, b->ev, za, tiles, st2); }));
+      PassArgs xa = za;
+      xa.in = w.T[k];
+      xa.out = w.T[k];
+      xa.power = power;
+      OS3D_CK(counted_launch(OS3D_KIND_XY_SOFT, st2,
+                             [&] { return launch_plane_soft(b, xa, st2); }));
+      PassArgs zi = za;
+      zi.in = w.T[k];
+      zi.out = w.A[k];
+      zi.accumulate = b->p.overlap ? q >= 2 : q >= 1;
+      OS3D_CK(counted_launch(OS3D_KIND_Z_INV_SCORE, st2,
+                             [&] { return launch_z(nz, Z_INV_SCORE, b->ev, zi, tiles, st2); }));
+    }
+    if (b->p.overlap) OS3D_CK(join_side(b, s));
+    const os3d_status st3 = finish_real(b, w, q, b->GM, fout, v, s);
+    if (st3 != OS3D_OK) return st3;
+  }
+  return OS3D_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+os3d_status os3d_forward(const os3d_bank* b, const float* f, int batch, void* U,
+                         os3d_udtype udtype, void* ws, void* stream) {
+  const os3d_status st = check_call(b, f, U, batch, udtype, ws);
+  if (st != OS3D_OK) return st;
+  return forward_impl(b, f, batch, U, udtype, ws, (cudaStream_t)stream);
+}
+
 os3d_status os3d_inverse(const os3d_bank* b, const void* U, os3d_udtype udtype, int batch,
                          float* f_out, void* ws, void* stream) {
   const os3d_status st = check_call(b, U, f_out, batch, udtype, ws);
@@ -873,6 +995,64 @@ os3d_status os3d_adjoint(const os3d_bank* b, const void* G, os3d_udtype udtype, 
   const os3d_status st = check_call(b, G, grad_f, batch, udtype, ws);
   if (st != OS3D_OK) return st;
   return backward_impl(b, G, udtype, batch, grad_f, ws, (cudaStream_t)stream, false);
+}
+
+os3d_status os3d_approx_reconstruct(const os3d_bank* b, const void* U, os3d_udtype udtype,
+                                    int batch, float* f_out, void* stream) {
+  const os3d_status st = check_call(b, U, f_out, batch, udtype, nullptr);
+  if (st != OS3D_OK) return st;
+  const double c0 = b->c[0];
+  if (!(std::fabs(c0) > 0.0) || !std::isfinite(c0)) return OS3D_EINVAL;
+  const float wgt = (float)(1.0 / (b->n_o * c0));
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t eb = u_elem_bytes(udtype);
+  for (int v = 0; v < batch; ++v) {
+    const char* Uv = (const char*)U + (size_t)v * b->n_o * b->nvox * eb;
+    float* fv = f_out + (size_t)v * b->nvox;
+    OS3D_CK(counted_launch(OS3D_KIND_APPROX, s, [&] {
+      return launch_approx_sum(Uv, udtype == OS3D_U_BF16X2, b->n_o, b->nvox, wgt, fv, s);
+    }));
+  }
+  return OS3D_OK;
+}
+
+os3d_status os3d_project(const os3d_bank* b, const void* U, os3d_udtype udtype, int batch,
+                         void* U_out, void* ws, void* stream) {
+  os3d_status st = check_call(b, U, U_out, batch, udtype, ws);
+  if (st != OS3D_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  // the reconstructed image lives in the second block intermediate of the
+  // workspace, which neither transform touches while it is needed
+  float* fs = reinterpret_cast<float*>(carve(b, ws).T[1]);
+  const size_t vb = (size_t)b->n_o * b->nvox * u_elem_bytes(udtype);
+  for (int v = 0; v < batch; ++v) {
+    st = backward_impl(b, (const char*)U + v * vb, udtype, 1, fs, ws, s, true);
+    if (st == OS3D_OK) st = forward_impl(b, fs, 1, (char*)U_out + v * vb, udtype, ws, s);
+    if (st != OS3D_OK) return st;
+  }
+  return OS3D_OK;
+}
+
+os3d_status os3d_soft_threshold(const void* in, void* out, os3d_udtype udtype, long long count,
+                                double power, void* stream) {
+  if (!in || !out || count < 0 || count % 4 != 0) return OS3D_EINVAL;
+  if (udtype != OS3D_U_C64 && udtype != OS3D_U_BF16X2) return OS3D_EINVAL;
+  if (!(power > 0.0) || !std::isfinite(power)) return OS3D_EINVAL;
+  if ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(out)) & 15) return OS3D_EINVAL;
+  if (count == 0) return OS3D_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  OS3D_CK(counted_launch(OS3D_KIND_SOFT, s, [&] {
+    return launch_soft_scores(in, out, udtype == OS3D_U_BF16X2, count, (float)power, s);
+  }));
+  return OS3D_OK;
+}
+
+os3d_status os3d_upsilon(const os3d_bank* b, const float* f, int batch, float* f_out,
+                         double power, void* ws, void* stream) {
+  const os3d_status st = check_call(b, f, f_out, batch, OS3D_U_C64, ws);
+  if (st != OS3D_OK) return st;
+  if (!(power > 0.0) || !std::isfinite(power)) return OS3D_EINVAL;
+  return upsilon_impl(b, f, batch, f_out, (float)power, ws, (cudaStream_t)stream);
 }
 
 }  // extern "C"
@@ -1015,9 +1195,9 @@ os3d_status os3d_profile_reset(void) {
 }
 
 const char* os3d_kernel_kind_name(int kind) {
-  static const char* names[OS3D_KIND_COUNT] = {"xy_fwd_real", "xy_fwd_score", "xy_inv_score",
-                                                "xy_inv_real", "z_fwd_prep", "z_fwd_score",
-                                                "z_inv_score", "z_inv_final"};
+  static const char* names[OS3D_KIND_COUNT] = {
+      "xy_fwd_real", "xy_fwd_score", "xy_inv_score", "xy_inv_real", "z_fwd_prep", "z_fwd_score",
+      "z_inv_score", "z_inv_final", "xy_soft", "approx_sum", "soft_threshold"};
   return (kind >= 0 && kind < OS3D_KIND_COUNT) ? names[kind] : "unknown";
 }
 

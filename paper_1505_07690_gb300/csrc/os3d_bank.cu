@@ -40,7 +40,7 @@ __device__ double bspline_dev(double x, int k) {
 //  mode 0: projection b_l = (2l+1)/2 sum_p w_p A(theta_p) P_l(z_p).
 __global__ void __launch_bounds__(kFitThreads)
 fit_kernel(const double* __restrict__ zt, const double* __restrict__ wt, int npts, int mode,
-           int k, double s_theta, int L, int n_o, double* __restrict__ out) {
+           int k, double s_theta, int L, int n_o, int profile, double* __restrict__ out) {
   __shared__ double P[kFitChunk][kMaxL + 2];
   __shared__ double Gm[(kMaxL + 1) * (kMaxL + 1)];
   __shared__ double rv[kMaxL + 1];
@@ -125,12 +125,15 @@ fit_kernel(const double* __restrict__ zt, const double* __restrict__ wt, int npt
       b[i] = s / Gm[i * nl + i];
     }
   }
-  // Funk transform c^e_l = 2 pi P_l(0) b_l and anti-symmetrisation
-  // c^o_l = (1 - (-1)^l) b_l (Sec. 3.2); then kappa (M averages to one).
+  // cake wavelet (profile 0): Funk transform c^e_l = 2 pi P_l(0) b_l and
+  // anti-symmetrisation c^o_l = (1 - (-1)^l) b_l (Sec. 3.2); plate detector
+  // (profile 1): h = A, c_l = b_l (Sec. 3.1). Then kappa (M averages to one).
   double c[kMaxL + 1];
   double p0 = 1.0;   // P_l(0): P_{l+2}(0) = -(l+1)/(l+2) P_l(0)
   for (int l = 0; l <= L; ++l) {
-    if (l % 2 == 0) {
+    if (profile == 1) {
+      c[l] = b[l];
+    } else if (l % 2 == 0) {
       c[l] = 2.0 * kPiD * p0 * b[l];
       p0 = -p0 * (l + 1) / (l + 2);
     } else {
@@ -240,8 +243,9 @@ bank_M_kernel(int nz, int ny, int nx, int N, double tscale, double eps,
 }  // namespace
 
 cudaError_t launch_fit(const double* d_zt, const double* d_w, int npts, int mode, int k,
-                       double s_theta, int L, int n_o, double* d_out, cudaStream_t s) {
-  fit_kernel<<<1, kFitThreads, 0, s>>>(d_zt, d_w, npts, mode, k, s_theta, L, n_o, d_out);
+                       double s_theta, int L, int n_o, int profile, double* d_out,
+                       cudaStream_t s) {
+  fit_kernel<<<1, kFitThreads, 0, s>>>(d_zt, d_w, npts, mode, k, s_theta, L, n_o, profile, d_out);
   return cudaGetLastError();
 }
 

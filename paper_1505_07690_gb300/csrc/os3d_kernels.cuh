@@ -31,7 +31,9 @@ enum ZMode { Z_FWD_PREP = 0, Z_FWD_SCORE = 1, Z_INV_SCORE = 2, Z_INV_FINAL = 3 }
 //  XY_FWD_SCORE: T_s -> IDFT_xy -> U_a, U_b = conj U_a              (HBM store)
 //  XY_INV_SCORE: U_a + conj U_b (HBM load) -> DFT_xy               -> T_s
 //  XY_INV_REAL : T0 -> IDFT_xy -> real part                        -> f
-enum XYMode { XY_FWD_REAL = 0, XY_FWD_SCORE = 1, XY_INV_SCORE = 2, XY_INV_REAL = 3 };
+//  XY_SOFT     : T_s -> IDFT_xy -> m_s Phi(.) -> DFT_xy             -> T_s (in place)
+//                (Phi the soft threshold |u|^p sgn(u) per part, m_s = 2 for a pair)
+enum XYMode { XY_FWD_REAL = 0, XY_FWD_SCORE = 1, XY_INV_SCORE = 2, XY_INV_REAL = 3, XY_SOFT = 4 };
 
 struct PassArgs {
   const void* in;
@@ -47,6 +49,7 @@ struct PassArgs {
   float wz, wy, wx;           // 2 pi / n per axis
   int nslots;
   int accumulate;             // Z_INV_SCORE: 0 -> A = sum, 1 -> A += sum
+  float power;                // XY_SOFT / soft threshold: exponent p > 0
   float nvec[kMaxSlots][3];   // orientation n_a (x, y, z) of each slot
   HEval h;
 };
@@ -73,9 +76,27 @@ cudaError_t launch_xy(int ny, int nx, int mode, int ubf16, const PassArgs& a, cu
 bool xy_supported(int ny, int nx);
 bool z_supported(int nz);
 
+// Soft threshold Phi(u) = |u|^p sgn(u) of one real number (Sec. 4.1); the
+// common exponent 1.5 as |u| sqrt(|u|).
+__device__ __forceinline__ float soft_part(float u, float p) {
+  const float m = fabsf(u);
+  const float r = (p == 1.5f) ? m * sqrtf(m) : (p == 1.0f ? m : powf(m, p));
+  return copysignf(r, u);
+}
+
+// elementwise kernels (os3d_elementwise.cu)
+cudaError_t launch_approx_sum(const void* U, int ubf16, int n_o, long long nvox, float w,
+                              float* out, cudaStream_t s);
+cudaError_t launch_soft_scores(const void* in, void* out, int ubf16, long long count,
+                               float power, cudaStream_t s);
+// in place on a.nslots volumes of a.out, a.slot_stride apart, nvox each;
+// slot s scaled by 2 when a.ub[s] >= 0 (an antipodal pair)
+cudaError_t launch_soft_slots(const PassArgs& a, long long nvox, cudaStream_t s);
+
 // FP64 bank kernels
 cudaError_t launch_fit(const double* d_z, const double* d_w, int npts, int mode, int k,
-                       double s_theta, int L, int n_o, double* d_out, cudaStream_t s);
+                       double s_theta, int L, int n_o, int profile, double* d_out,
+                       cudaStream_t s);
 cudaError_t launch_bank_M(int nz, int ny, int nx, int N, double gamma, double eps,
                           const double* d_c, int L, const double* d_slots, int nslots,
                           int n_o, float* Gs, float* GM, float* Minv, cudaStream_t s);

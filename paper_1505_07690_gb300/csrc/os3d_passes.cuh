@@ -491,6 +491,229 @@ xy_kernel(const __grid_constant__ PassArgs a) {
 }
 
 // ----------------------------------------------------------------------------
+// Score-domain step of Upsilon = W^{*,ext} Phi W (Sec. 4.1) for one block of
+// orientation pairs, fused into one plane pass, in place on T_s:
+//   T_s <- DFT_xy[ m_s Phi( IDFT_xy T_s ) ]
+// Phi is the soft threshold |u|^p sgn(u) of the real and imaginary parts;
+// m_s = 2 for an antipodal pair (the inverse takes V_a + conj V_b and Phi
+// commutes with conjugation, so V_b = conj V_a), 1 for an unpaired slot.
+// The score U_s = IDFT_xy T_s exists only in shared memory. Layout and
+// exchanges as xy_kernel: IDFT along x on this CTA's rows, exchange, IDFT
+// along y on its columns; the y step-2 outputs go back to the rows they were
+// read from (y index k1 + R1y k2 in row R2y k1 + k2), the DFT along y reads
+// them through that map, exchanges back to rows, and the DFT along x writes
+// T_s.
+// ----------------------------------------------------------------------------
+template <int NY, int NX>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(XYCfg<NY, NX>::NT, 2)
+xy_soft_kernel(const __grid_constant__ PassArgs a) {
+  using C = XYCfg<NY, NX>;
+  constexpr int R1x = C::R1x, R2x = C::R2x, R1y = C::R1y, R2y = C::R2y;
+  constexpr int NT = C::NT, NYH = C::NYH, NXH = C::NXH;
+
+  extern __shared__ __align__(16) float2 sm[];
+  float2* work = sm;
+  float2* twx = sm + C::BUF;   // exp(+2 pi i m / NX); the DFT uses the conjugates
+  float2* twy = twx + NX;
+
+  const int t = threadIdx.x;
+  const int h = (int)cluster_rank();
+  const unsigned peer_base = map_cluster_rank(smem_addr(work), (unsigned)(h ^ 1));
+  const long long P = (long long)NY * NX;
+  const int cl = blockIdx.x >> 1, ncl = gridDim.x >> 1;
+  const int nunits = a.nz * a.nslots;
+  // row of the y-layout that holds y index n after the IDFT along y
+  auto yrow = [](int n) { return R2y * (n % R1y) + n / R1y; };
+
+  fill_twiddles<NX, +1>(twx);
+  fill_twiddles<NY, +1>(twy);
+  __syncthreads();
+
+  for (int u = cl; u < nunits; u += ncl) {
+    const int z = u % a.nz, s = u / a.nz;
+    float2* T = reinterpret_cast<float2*>(a.out) + (long long)s * a.slot_stride + (long long)z * P;
+    const float scale = a.ub[s] >= 0 ? 2.f : 1.f;
+    // ---- (1) IDFT along x, step 1 (global -> registers -> shared)
+    {
+      const int n2 = t % R2x, r0 = t / R2x;
+      float2 tw[R1x];
+#pragma unroll
+      for (int k1 = 0; k1 < R1x; ++k1) tw[k1] = twx[(n2 * k1) % NX];
+#pragma unroll
+      for (int j = 0; j < C::JX1; ++j) {
+        const int r = r0 + (NT / R2x) * j;
+        const float2* row = T + (long long)(h * NYH + r) * NX;
+        float2 v[R1x];
+#pragma unroll
+        for (int n1 = 0; n1 < R1x; ++n1) v[n1] = row[n2 + R2x * n1];
+        dft<R1x, +1>(v);
+#pragma unroll
+        for (int k1 = 0; k1 < R1x; ++k1)
+          work[C::xphys(r, n2 + R2x * k1)] = (k1 == 0) ? v[k1] : cmul(v[k1], tw[k1]);
+      }
+    }
+    __syncthreads();
+    // ---- (2) IDFT along x, step 2; outputs to the owner of their column
+    {
+      float2 w[C::JX3][R2x];
+#pragma unroll
+      for (int j = 0; j < C::JX3; ++j) {
+        int r, k1;
+        C::x2_item(t, j, r, k1);
+#pragma unroll
+        for (int m = 0; m < R2x; ++m) w[j][m] = work[C::xphys(r, m + R2x * k1)];
+        dft<R2x, +1>(w[j]);
+      }
+      cluster_sync_acqrel();   // both halves have read their x layouts
+#pragma unroll
+      for (int j = 0; j < C::JX3; ++j) {
+        int r, k1;
+        C::x2_item(t, j, r, k1);
+        const int row = (h * NYH + r) * C::PY;
+#pragma unroll
+        for (int k2 = 0; k2 < R2x; ++k2) {
+          const int c = k1 + R1x * k2;
+          const int owner = (NXH % R1x == 0) ? (k2 >= NXH / R1x) : (c >= NXH);
+          const int idx = row + c - owner * NXH;
+          if (owner == h) work[idx] = w[j][k2];
+          else st_cluster_f2(peer_base + 8u * (unsigned)idx, w[j][k2]);
+        }
+      }
+      cluster_sync_acqrel();   // this CTA's y layout is complete
+    }
+    // ---- (3) IDFT along y, step 1 (in place)
+    {
+      const int n2 = t / C::CW;
+      float2 tw[R1y];
+#pragma unroll
+      for (int k1 = 0; k1 < R1y; ++k1) tw[k1] = twy[(n2 * k1) % NY];
+#pragma unroll
+      for (int j = 0; j < C::JY1; ++j) {
+        const int c = t % C::CW + C::CW * j;
+        float2 u1[R1y];
+#pragma unroll
+        for (int n1 = 0; n1 < R1y; ++n1) u1[n1] = work[(n2 + R2y * n1) * C::PY + c];
+        dft<R1y, +1>(u1);
+#pragma unroll
+        for (int k1 = 0; k1 < R1y; ++k1)
+          work[(n2 + R2y * k1) * C::PY + c] = (k1 == 0) ? u1[k1] : cmul(u1[k1], tw[k1]);
+      }
+    }
+    __syncthreads();
+    // ---- (4) IDFT along y, step 2: U_s; m_s Phi(U_s) back into the rows read
+#pragma unroll
+    for (int j = 0; j < C::JY3; ++j) {
+      const int q = t + NT * j;
+      const int c = q % NXH, k1 = q / NXH;
+      float2 w[R2y];
+#pragma unroll
+      for (int m = 0; m < R2y; ++m) w[m] = work[(m + R2y * k1) * C::PY + c];
+      dft<R2y, +1>(w);
+#pragma unroll
+      for (int k2 = 0; k2 < R2y; ++k2)
+        work[(R2y * k1 + k2) * C::PY + c] =
+            make_float2(scale * soft_part(w[k2].x, a.power), scale * soft_part(w[k2].y, a.power));
+    }
+    __syncthreads();
+    // ---- (5) DFT along y, step 1 (in place through the row map)
+    {
+      const int n2 = t / C::CW;
+      float2 tw[R1y];
+#pragma unroll
+      for (int k1 = 0; k1 < R1y; ++k1) tw[k1] = cconj(twy[(n2 * k1) % NY]);
+#pragma unroll
+      for (int j = 0; j < C::JY1; ++j) {
+        const int c = t % C::CW + C::CW * j;
+        float2 u1[R1y];
+#pragma unroll
+        for (int n1 = 0; n1 < R1y; ++n1) u1[n1] = work[yrow(n2 + R2y * n1) * C::PY + c];
+        dft<R1y, -1>(u1);
+#pragma unroll
+        for (int k1 = 0; k1 < R1y; ++k1)
+          work[yrow(n2 + R2y * k1) * C::PY + c] = (k1 == 0) ? u1[k1] : cmul(u1[k1], tw[k1]);
+      }
+    }
+    __syncthreads();
+    // ---- (6) DFT along y, step 2; outputs to the owner of their row
+    {
+      float2 w[C::JY3][R2y];
+#pragma unroll
+      for (int j = 0; j < C::JY3; ++j) {
+        const int q = t + NT * j;
+        const int c = q % NXH, k1 = q / NXH;
+#pragma unroll
+        for (int m = 0; m < R2y; ++m) w[j][m] = work[yrow(m + R2y * k1) * C::PY + c];
+        dft<R2y, -1>(w[j]);
+      }
+      cluster_sync_acqrel();   // both halves have read their y layouts
+#pragma unroll
+      for (int j = 0; j < C::JY3; ++j) {
+        const int q = t + NT * j;
+        const int c = q % NXH, k1 = q / NXH;
+#pragma unroll
+        for (int k2 = 0; k2 < R2y; ++k2) {
+          const int ky = k1 + R1y * k2;
+          const int owner = ky >= NYH;
+          const int idx = C::xphys(ky - owner * NYH, h * NXH + c);
+          if (owner == h) work[idx] = w[j][k2];
+          else st_cluster_f2(peer_base + 8u * (unsigned)idx, w[j][k2]);
+        }
+      }
+      cluster_sync_acqrel();   // this CTA's x layout is complete
+    }
+    // ---- (7) DFT along x, step 1 (in place on this CTA's rows)
+    {
+      const int n2 = t % R2x, r0 = t / R2x;
+      float2 tw[R1x];
+#pragma unroll
+      for (int k1 = 0; k1 < R1x; ++k1) tw[k1] = cconj(twx[(n2 * k1) % NX]);
+#pragma unroll
+      for (int j = 0; j < C::JX1; ++j) {
+        const int r = r0 + (NT / R2x) * j;
+        float2 v[R1x];
+#pragma unroll
+        for (int n1 = 0; n1 < R1x; ++n1) v[n1] = work[C::xphys(r, n2 + R2x * n1)];
+        dft<R1x, -1>(v);
+#pragma unroll
+        for (int k1 = 0; k1 < R1x; ++k1)
+          work[C::xphys(r, n2 + R2x * k1)] = (k1 == 0) ? v[k1] : cmul(v[k1], tw[k1]);
+      }
+    }
+    __syncthreads();
+    // ---- (8) DFT along x, step 2 -> T_s
+#pragma unroll
+    for (int j = 0; j < C::JX3; ++j) {
+      int r, k1;
+      C::x2_item(t, j, r, k1);
+      float2 w[R2x];
+#pragma unroll
+      for (int m = 0; m < R2x; ++m) w[m] = work[C::xphys(r, m + R2x * k1)];
+      dft<R2x, -1>(w);
+      float2* row = T + (long long)(h * NYH + r) * NX;
+#pragma unroll
+      for (int k2 = 0; k2 < R2x; ++k2) row[k1 + R1x * k2] = w[k2];
+    }
+    __syncthreads();    // work is rewritten by the next unit
+  }
+  cluster_sync_acqrel();   // no CTA leaves while its peer may still write into it
+}
+
+template <int NY, int NX>
+cudaError_t launch_xy_soft_one(const PassArgs& a, cudaStream_t s) {
+  using C = XYCfg<NY, NX>;
+  auto k = xy_soft_kernel<NY, NX>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)C::smem_bytes);
+  if (e != cudaSuccess) return e;
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const int clusters = std::max(1, std::min(a.nz * a.nslots, nsm));
+  k<<<2 * clusters, C::NT, C::smem_bytes, s>>>(a);
+  return cudaGetLastError();
+}
+
+// ----------------------------------------------------------------------------
 // per-size launchers
 // ----------------------------------------------------------------------------
 template <int NZ>
@@ -542,6 +765,7 @@ cudaError_t launch_xy_n(int mode, int ub, const PassArgs& a, cudaStream_t s) {
     case XY_INV_SCORE:
       return ub ? launch_xy_one<NY, NX, XY_INV_SCORE, 1>(a, s)
                 : launch_xy_one<NY, NX, XY_INV_SCORE, 0>(a, s);
+    case XY_SOFT: return launch_xy_soft_one<NY, NX>(a, s);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -25,7 +25,7 @@ class os3d_params(ctypes.Structure):
     _fields_ = [("k", ctypes.c_int), ("s_theta", ctypes.c_double), ("L", ctypes.c_int),
                 ("N", ctypes.c_int), ("gamma", ctypes.c_double), ("eps", ctypes.c_double),
                 ("fit_mode", ctypes.c_int), ("block_slots", ctypes.c_int),
-                ("overlap", ctypes.c_int)]
+                ("overlap", ctypes.c_int), ("profile", ctypes.c_int)]
 
 
 class os3d_server_config(ctypes.Structure):
@@ -55,6 +55,11 @@ def lib():
         L.os3d_status_string.argtypes = [i]
         L.os3d_default_params.argtypes = [ctypes.POINTER(os3d_params)]
         L.os3d_icosa_orientations.argtypes = [i, ctypes.POINTER(d), i, ctypes.POINTER(i)]
+        L.os3d_octa_orientations.argtypes = [i, ctypes.POINTER(d), i, ctypes.POINTER(i)]
+        L.os3d_approx_reconstruct.argtypes = [vp, vp, i, i, vp, vp]
+        L.os3d_project.argtypes = [vp, vp, i, i, vp, vp, vp]
+        L.os3d_soft_threshold.argtypes = [vp, vp, i, ctypes.c_longlong, d, vp]
+        L.os3d_upsilon.argtypes = [vp, vp, i, vp, d, vp, vp]
         L.os3d_make_wavelets.argtypes = [ctypes.POINTER(i), ctypes.POINTER(d), i,
                                          ctypes.POINTER(os3d_params), vp, ctypes.POINTER(vp)]
         L.os3d_forward.argtypes = [vp, vp, i, vp, i, vp, vp]
@@ -86,7 +91,9 @@ def lib():
                      "os3d_profile_enable", "os3d_profile_read", "os3d_profile_reset",
                      "os3d_forward_static", "os3d_server_default_config",
                      "os3d_server_create", "os3d_server_submit", "os3d_server_wait",
-                     "os3d_server_destroy"):
+                     "os3d_server_destroy", "os3d_octa_orientations",
+                     "os3d_approx_reconstruct", "os3d_project", "os3d_soft_threshold",
+                     "os3d_upsilon"):
             getattr(L, name).restype = i
         _lib = L
     return _lib
@@ -118,15 +125,23 @@ def os3d_default_params(**overrides) -> os3d_params:
     return p
 
 
-def os3d_icosa_orientations(subdiv: int) -> np.ndarray:
+def _orientations(fn, name, subdiv):
     n = ctypes.c_int(0)
-    lib().os3d_icosa_orientations(int(subdiv), None, 0, ctypes.byref(n))
+    fn(int(subdiv), None, 0, ctypes.byref(n))
     if n.value <= 0:
-        raise OS3DError(1, "os3d_icosa_orientations")
+        raise OS3DError(1, name)
     out = np.zeros((n.value, 3), dtype=np.float64)
-    _check(lib().os3d_icosa_orientations(int(subdiv), out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
-                                         n.value, ctypes.byref(n)), "os3d_icosa_orientations")
+    _check(fn(int(subdiv), out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), n.value,
+              ctypes.byref(n)), name)
     return out
+
+
+def os3d_icosa_orientations(subdiv: int) -> np.ndarray:
+    return _orientations(lib().os3d_icosa_orientations, "os3d_icosa_orientations", subdiv)
+
+
+def os3d_octa_orientations(subdiv: int) -> np.ndarray:
+    return _orientations(lib().os3d_octa_orientations, "os3d_octa_orientations", subdiv)
 
 
 class Bank:
@@ -278,7 +293,68 @@ def os3d_adjoint(bank: Bank, G, grad_f=None, workspace=None, stream=None):
     return _backward(lib().os3d_adjoint, "os3d_adjoint", bank, G, grad_f, workspace, stream)
 
 
-OS3D_KIND_COUNT = 8
+def os3d_approx_reconstruct(bank: Bank, U, f_out=None, stream=None):
+    """Approximate reconstruction Re sum_i U_i / (N_o c_0)
+    (Eq. Reconstruction2Approximation)."""
+    import torch
+    ud, batch = _check_score(bank, U)
+    if f_out is None:
+        f_out = torch.empty((batch,) + bank.dims, dtype=torch.float32, device="cuda")
+    if not (f_out.is_cuda and f_out.dtype == torch.float32 and f_out.is_contiguous()
+            and f_out.numel() == batch * int(np.prod(bank.dims))):
+        raise ValueError("output must be a contiguous float32 CUDA tensor of the batch's size")
+    _check(lib().os3d_approx_reconstruct(bank.handle, _ptr(U), ud, batch, _ptr(f_out),
+                                         _stream(stream)), "os3d_approx_reconstruct")
+    return f_out
+
+
+def os3d_project(bank: Bank, U, U_out=None, workspace=None, stream=None):
+    """P_psi U = W W^{*,ext} U (App. A); U_out may be U."""
+    import torch
+    ud, batch = _check_score(bank, U)
+    if U_out is None:
+        U_out = torch.empty_like(U)
+    ud2, b2 = _check_score(bank, U_out)
+    if ud2 != ud or b2 != batch:
+        raise ValueError("U_out must match U")
+    _check(lib().os3d_project(bank.handle, _ptr(U), ud, batch, _ptr(U_out), _ws_ptr(workspace),
+                              _stream(stream)), "os3d_project")
+    return U_out
+
+
+def os3d_soft_threshold(U, power: float = 1.5, out=None, stream=None):
+    """Phi(U) = |U|^p sgn(U) per real and imaginary part (Sec. 4.1); out may be U."""
+    import torch
+    ud = _udtype(U)
+    if not (U.is_cuda and U.is_contiguous()):
+        raise ValueError("U must be a contiguous CUDA tensor")
+    if out is None:
+        out = torch.empty_like(U)
+    if out.dtype != U.dtype or out.shape != U.shape or not out.is_contiguous():
+        raise ValueError("out must match U")
+    count = U.numel() // 2 if ud == OS3D_U_BF16X2 else U.numel()
+    _check(lib().os3d_soft_threshold(_ptr(U), _ptr(out), ud, count, float(power), _stream(stream)),
+           "os3d_soft_threshold")
+    return out
+
+
+def os3d_upsilon(bank: Bank, f, power: float = 1.5, f_out=None, workspace=None, stream=None):
+    """Upsilon f = W^{*,ext} Phi W f (Sec. 4.1) without storing the score."""
+    import torch
+    if not (f.is_cuda and f.dtype == torch.float32 and f.is_contiguous()):
+        raise ValueError("f must be a contiguous float32 CUDA tensor")
+    batch = _batch_of(f, 3, bank.dims)
+    if f_out is None:
+        f_out = torch.empty_like(f)
+    if not (f_out.is_cuda and f_out.dtype == torch.float32 and f_out.is_contiguous()
+            and f_out.numel() == f.numel()):
+        raise ValueError("f_out must be a contiguous float32 CUDA tensor like f")
+    _check(lib().os3d_upsilon(bank.handle, _ptr(f), batch, _ptr(f_out), float(power),
+                              _ws_ptr(workspace), _stream(stream)), "os3d_upsilon")
+    return f_out
+
+
+OS3D_KIND_COUNT = 11
 
 
 def os3d_launch_count() -> int:

@@ -37,6 +37,17 @@ def test_orientations_match_oracle(L):
         assert np.abs(a - b).max() < 1e-12
 
 
+def test_octahedral_orientations_match_oracle(L):
+    from paper_1505_07690_gb300 import os3d
+    for s in (0, 1, 2, 3):
+        a = os3d.os3d_octa_orientations(s)
+        b = O.octa_orientations(s)
+        assert a.shape == b.shape
+        assert np.abs(a - b).max() < 1e-12
+    n = ctypes.c_int(0)
+    assert L.os3d_octa_orientations(6, None, 0, ctypes.byref(n)) == 1
+
+
 def test_orientation_capacity_and_range(L):
     n = ctypes.c_int(0)
     buf = (ctypes.c_double * 30)()
@@ -69,7 +80,7 @@ def test_argument_errors_before_any_launch(L):
                                 ctypes.byref(p), None, ctypes.byref(h)) == 1
     # parameters out of range
     for field, val in (("L", 33), ("eps", 0.0), ("gamma", 1.0), ("k", 9), ("fit_mode", 2),
-                       ("s_theta", -1.0), ("block_slots", 9)):
+                       ("s_theta", -1.0), ("block_slots", 9), ("profile", 2)):
         q = os3d.os3d_default_params(**{field: val})
         assert L.os3d_make_wavelets(dims, Vp, 42, ctypes.byref(q), None, ctypes.byref(h)) == 1, field
     # grid without a compiled plan
@@ -83,6 +94,19 @@ def test_argument_errors_before_any_launch(L):
     assert L.os3d_adjoint(None, None, 0, 1, None, None, None) == 1
     assert L.os3d_bank_info(None, None, None) == 1
     assert L.os3d_destroy_bank(None) == 1
+    assert L.os3d_approx_reconstruct(None, None, 0, 1, None, None) == 1
+    assert L.os3d_project(None, None, 0, 1, None, None, None) == 1
+    assert L.os3d_upsilon(None, None, 1, None, 1.5, None, None) == 1
+    # soft threshold: pointers, count, alignment and exponent are checked first
+    buf = ctypes.create_string_buffer(64)
+    a16 = (ctypes.addressof(buf) + 15) // 16 * 16
+    assert L.os3d_soft_threshold(None, None, 0, 4, 1.5, None) == 1
+    assert L.os3d_soft_threshold(a16, a16, 0, 6, 1.5, None) == 1       # not a multiple of 4
+    assert L.os3d_soft_threshold(a16 + 8, a16 + 8, 0, 4, 1.5, None) == 1  # misaligned
+    for pw in (0.0, -1.0, float("inf"), float("nan")):
+        assert L.os3d_soft_threshold(a16, a16, 0, 4, pw, None) == 1
+    assert L.os3d_soft_threshold(a16, a16, 2, 4, 1.5, None) == 1       # unknown udtype
+    assert L.os3d_soft_threshold(a16, a16, 0, 0, 1.5, None) == 0       # nothing to do
 
 
 def test_injected_allocation_failure(L, monkeypatch):

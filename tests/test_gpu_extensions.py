@@ -1,0 +1,208 @@
+"""GPU parity of the extensions through the C ABI against the FP64 oracle:
+the plate-detector profile, the octahedral orientation sets, the approximate
+reconstruction, the projection P_psi, the soft threshold and the fused
+Upsilon = W^{*,ext} Phi W. Tolerances as in test_gpu_parity.py: relative L2
+error <= 1e-5 for FP32 results, 5e-3 where a score is stored in BF16."""
+import numpy as np
+import pytest
+
+from oracle import os3d_oracle as O
+from paper_1505_07690_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+TOL_BF16 = 5e-3
+
+
+def rel(a, b):
+    a = np.asarray(a)
+    b = np.asarray(b)
+    return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
+
+
+@pytest.fixture(scope="module")
+def M():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1505_07690_gb300 import build, os3d
+    build.build()
+    return os3d
+
+
+def _pair(M, dims, V, **kw):
+    p = M.os3d_default_params(**kw)
+    bank = M.os3d_make_wavelets(dims, V, p)
+    ob = O.Bank(dims, V, O.Params(k=p.k, s_theta=p.s_theta, L=p.L, N=p.N, gamma=p.gamma,
+                                  eps=p.eps, fit_mode=p.fit_mode, profile=p.profile))
+    return bank, ob
+
+
+def _np(t):
+    import torch
+    torch.cuda.synchronize()
+    return t.detach().cpu().numpy()
+
+
+def _cuda(x):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def _c64(U):
+    return _cuda(np.asarray(U).astype(np.complex64))
+
+
+# ---------------------------------------------------------------------------
+# wavelet variants (Sec. 3.1 plate detector, Sec. 2.1 octahedral sampling)
+# ---------------------------------------------------------------------------
+def test_plate_profile_fig3_parameters(M):
+    """h = A with the parameters of Fig. 3 (L = 16, s_theta = 0.6, k = 2,
+    N = 20, gamma = 0.8; the clamp binds near rho_N)."""
+    dims = (32, 32, 32)
+    V = O.icosa_orientations(1)
+    bank, ob = _pair(M, dims, V, profile=1, L=16, s_theta=0.6, N=20, gamma=0.8)
+    b, c = M.os3d_bank_coefficients(bank)
+    assert np.abs(c - ob.c).max() <= 1e-10 * np.abs(ob.c).max()
+    f = synth.straight_tubes(dims, 3, seed=21)
+    U = M.os3d_forward(bank, _cuda(f))
+    Uo = O.forward(f, ob)
+    assert rel(_np(U)[0], Uo) <= TOL
+    assert rel(_np(M.os3d_inverse(bank, U))[0], O.inverse(Uo, ob)) <= TOL
+
+
+@pytest.mark.parametrize("dims,subdiv", [((32, 32, 32), 1), ((16, 16, 16), 2), ((32, 48, 64), 1)])
+def test_octahedral_sets(M, dims, subdiv):
+    V = O.octa_orientations(subdiv)
+    assert np.abs(M.os3d_octa_orientations(subdiv) - V).max() < 1e-12
+    bank, ob = _pair(M, dims, V, L=12, block_slots=4)
+    f = synth.straight_tubes(dims, 2, seed=22, noise=0.1)
+    U = M.os3d_forward(bank, _cuda(f))
+    Uo = O.forward(f, ob)
+    assert rel(_np(U)[0], Uo) <= TOL
+    assert rel(_np(M.os3d_inverse(bank, U))[0], O.inverse(Uo, ob)) <= TOL
+
+
+# ---------------------------------------------------------------------------
+# approximate reconstruction and projection
+# ---------------------------------------------------------------------------
+def test_approximate_reconstruction(M):
+    dims = (32, 32, 32)
+    bank, ob = _pair(M, dims, O.icosa_orientations(1), L=12)
+    rng = np.random.default_rng(23)
+    G = (rng.standard_normal((2, 42) + dims) + 1j * rng.standard_normal((2, 42) + dims))
+    fa = _np(M.os3d_approx_reconstruct(bank, _c64(G)))
+    for v in range(2):
+        assert rel(fa[v], O.approx_reconstruct(G[v].astype(np.complex64).astype(np.complex128), ob)) <= TOL
+    # on a score of an image, and from BF16 storage
+    f = synth.workload_volume("tubes32_no42")
+    Uo = O.forward(f, ob)
+    ref = O.approx_reconstruct(Uo, ob)
+    Ub = M.os3d_forward(bank, _cuda(f), bf16=True)
+    assert rel(_np(M.os3d_approx_reconstruct(bank, M.os3d_forward(bank, _cuda(f))))[0], ref) <= TOL
+    assert rel(_np(M.os3d_approx_reconstruct(bank, Ub))[0], ref) <= TOL_BF16
+
+
+def test_approximate_reconstruction_162_orientations(M):
+    dims = (64, 64, 64)
+    bank, ob = _pair(M, dims, O.icosa_orientations(2), L=16)
+    f = synth.spline_tubes(dims, 6, seed=24)
+    U = M.os3d_forward(bank, _cuda(f))
+    Uo = O.forward(f, ob)
+    assert rel(_np(M.os3d_approx_reconstruct(bank, U))[0], O.approx_reconstruct(Uo, ob)) <= TOL
+
+
+@pytest.mark.parametrize("dims", [(32, 32, 32), (32, 48, 64)])
+def test_projection(M, dims):
+    bank, ob = _pair(M, dims, O.icosa_orientations(1), L=12, block_slots=4)
+    rng = np.random.default_rng(25)
+    G = (rng.standard_normal((1, 42) + dims) + 1j * rng.standard_normal((1, 42) + dims))
+    G = G.astype(np.complex64)
+    Gd = _cuda(G)
+    P = _np(M.os3d_project(bank, Gd))[0]
+    Po = O.project(G[0].astype(np.complex128), ob)
+    assert rel(P, Po) <= TOL
+    # in place
+    M.os3d_project(bank, Gd, U_out=Gd)
+    assert rel(_np(Gd)[0], Po) <= TOL
+
+
+# ---------------------------------------------------------------------------
+# soft threshold and Upsilon (Sec. 4.1)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("power", [1.5, 2.0, 0.7])
+def test_soft_threshold(M, power):
+    import torch
+    rng = np.random.default_rng(26)
+    U = (rng.standard_normal((3, 7, 16)) + 1j * rng.standard_normal((3, 7, 16))).astype(np.complex64)
+    out = _np(M.os3d_soft_threshold(_cuda(U), power))
+    ref = O.soft_threshold(U.astype(np.complex128), power)
+    assert rel(out, ref) <= 1e-6
+    # bf16 storage, in place
+    Ub = torch.view_as_real(_cuda(U)).to(torch.bfloat16).contiguous()
+    Ur = Ub.float().cpu().numpy()
+    M.os3d_soft_threshold(Ub, power, out=Ub)
+    got = Ub.float().cpu().numpy()
+    exp = O.soft_threshold(Ur[..., 0] + 1j * Ur[..., 1], power)
+    assert rel(got[..., 0] + 1j * got[..., 1], exp) <= TOL_BF16
+
+
+def _upsilon_check(M, dims, V, f, power=1.5, **kw):
+    bank, ob = _pair(M, dims, V, **kw)
+    fu = _np(M.os3d_upsilon(bank, _cuda(f), power))
+    fb = f if f.ndim == 4 else f[None]
+    for v in range(fb.shape[0]):
+        assert rel(fu[v] if fu.ndim == 4 else fu, O.upsilon(fb[v], ob, power)) <= TOL
+    return bank, ob, fu
+
+
+def test_upsilon_cluster_path(M):
+    dims = (32, 32, 32)
+    f = synth.workload_volume("tubes32_no42")
+    _upsilon_check(M, dims, O.icosa_orientations(1), f, L=12)
+
+
+@pytest.mark.parametrize("bs,overlap", [(3, 1), (8, 0)])
+def test_upsilon_blocks_and_batch(M, bs, overlap):
+    dims = (32, 32, 32)
+    f = np.stack([synth.straight_tubes(dims, 3, seed=s) for s in (27, 28)])
+    _upsilon_check(M, dims, O.icosa_orientations(1), f, L=12, block_slots=bs, overlap=overlap)
+
+
+def test_upsilon_unpaired_and_pencil_grid(M):
+    """Orientations without antipodes (scale 1) on a grid that takes the
+    pencil passes and the separate soft-threshold kernel."""
+    dims = (32, 48, 64)
+    V = O.icosa_orientations(1)[:21].copy()
+    f = synth.straight_tubes(dims, 3, seed=29)
+    _upsilon_check(M, dims, V, f, L=12, block_slots=4)
+
+
+def test_upsilon_equals_the_composition(M):
+    """Fused Upsilon = os3d_forward, os3d_soft_threshold, os3d_inverse."""
+    dims = (64, 64, 64)
+    bank, ob = _pair(M, dims, O.icosa_orientations(2), L=16)
+    f = _cuda(synth.spline_tubes(dims, 6, seed=30))
+    fu = _np(M.os3d_upsilon(bank, f, 1.5))
+    U = M.os3d_forward(bank, f)
+    M.os3d_soft_threshold(U, 1.5, out=U)
+    fc = _np(M.os3d_inverse(bank, U))
+    assert rel(fu, fc) <= TOL
+
+
+def test_upsilon_headline_size_properties(M):
+    """128^3 spline tubes, 162 orientations, L = 16 (the benchmark's grid):
+    with p = 1 Upsilon is exactly the ball projection IDFT[1_ball f_hat];
+    with p = 1.5 it is positively homogeneous of degree 1.5 and odd."""
+    dims = (128, 128, 128)
+    f = synth.workload_volume("splines128_no162")
+    bank, ob = _pair(M, dims, O.icosa_orientations(2), L=16)
+    fd = _cuda(f)
+    wz, wy, wx = O.freq_grid(dims)
+    ball = np.sqrt(wz ** 2 + wy ** 2 + wx ** 2) < np.pi
+    fb = np.fft.ifftn(np.fft.fftn(f.astype(np.float64)) * ball).real
+    assert rel(_np(M.os3d_upsilon(bank, fd, 1.0)), fb) <= TOL
+    u = _np(M.os3d_upsilon(bank, fd, 1.5))
+    assert rel(_np(M.os3d_upsilon(bank, 4.0 * fd, 1.5)), 8.0 * u) <= TOL
+    assert rel(_np(M.os3d_upsilon(bank, -fd, 1.5)), -u) <= TOL
