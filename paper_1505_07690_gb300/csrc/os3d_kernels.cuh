@@ -76,11 +76,15 @@ cudaError_t launch_xy(int ny, int nx, int mode, int ubf16, const PassArgs& a, cu
 bool xy_supported(int ny, int nx);
 bool z_supported(int nz);
 
+// |u|^p for other exponents, kept out of line so that the unrolled DFT
+// kernels that call the soft threshold stay small
+static __device__ __noinline__ float soft_pow(float m, float p) { return powf(m, p); }
+
 // Soft threshold Phi(u) = |u|^p sgn(u) of one real number (Sec. 4.1); the
 // common exponent 1.5 as |u| sqrt(|u|).
 __device__ __forceinline__ float soft_part(float u, float p) {
   const float m = fabsf(u);
-  const float r = (p == 1.5f) ? m * sqrtf(m) : (p == 1.0f ? m : powf(m, p));
+  const float r = (p == 1.5f) ? m * sqrtf(m) : (p == 1.0f ? m : soft_pow(m, p));
   return copysignf(r, u);
 }
 

@@ -539,7 +539,7 @@ xy_soft_kernel(const __grid_constant__ PassArgs a) {
       float2 tw[R1x];
 #pragma unroll
       for (int k1 = 0; k1 < R1x; ++k1) tw[k1] = twx[(n2 * k1) % NX];
-#pragma unroll
+#pragma unroll 1
       for (int j = 0; j < C::JX1; ++j) {
         const int r = r0 + (NT / R2x) * j;
         const float2* row = T + (long long)(h * NYH + r) * NX;
@@ -587,7 +587,7 @@ xy_soft_kernel(const __grid_constant__ PassArgs a) {
       float2 tw[R1y];
 #pragma unroll
       for (int k1 = 0; k1 < R1y; ++k1) tw[k1] = twy[(n2 * k1) % NY];
-#pragma unroll
+#pragma unroll 1
       for (int j = 0; j < C::JY1; ++j) {
         const int c = t % C::CW + C::CW * j;
         float2 u1[R1y];
@@ -601,7 +601,7 @@ xy_soft_kernel(const __grid_constant__ PassArgs a) {
     }
     __syncthreads();
     // ---- (4) IDFT along y, step 2: U_s; m_s Phi(U_s) back into the rows read
-#pragma unroll
+#pragma unroll 1
     for (int j = 0; j < C::JY3; ++j) {
       const int q = t + NT * j;
       const int c = q % NXH, k1 = q / NXH;
@@ -621,7 +621,7 @@ xy_soft_kernel(const __grid_constant__ PassArgs a) {
       float2 tw[R1y];
 #pragma unroll
       for (int k1 = 0; k1 < R1y; ++k1) tw[k1] = cconj(twy[(n2 * k1) % NY]);
-#pragma unroll
+#pragma unroll 1
       for (int j = 0; j < C::JY1; ++j) {
         const int c = t % C::CW + C::CW * j;
         float2 u1[R1y];
@@ -667,7 +667,7 @@ xy_soft_kernel(const __grid_constant__ PassArgs a) {
       float2 tw[R1x];
 #pragma unroll
       for (int k1 = 0; k1 < R1x; ++k1) tw[k1] = cconj(twx[(n2 * k1) % NX]);
-#pragma unroll
+#pragma unroll 1
       for (int j = 0; j < C::JX1; ++j) {
         const int r = r0 + (NT / R2x) * j;
         float2 v[R1x];
@@ -681,7 +681,7 @@ xy_soft_kernel(const __grid_constant__ PassArgs a) {
     }
     __syncthreads();
     // ---- (8) DFT along x, step 2 -> T_s
-#pragma unroll
+#pragma unroll 1
     for (int j = 0; j < C::JX3; ++j) {
       int r, k1;
       C::x2_item(t, j, r, k1);
