@@ -12,8 +12,10 @@ product path. It shares no code, constants or tables with the CUDA side.
 
 Everything is float64 / complex128 numpy. Library primitives used as single
 steps: ``numpy.fft.fftn/ifftn`` (the DFT), ``numpy.linalg.pinv`` (the
-pseudo-inverse the paper names for the SH fit) and
-``numpy.polynomial.legendre.leggauss`` (Gauss-Legendre nodes).
+pseudo-inverse the paper names for the SH fit and the discrete
+Laplace-Beltrami operator), ``numpy.polynomial.legendre.leggauss``
+(Gauss-Legendre nodes), ``scipy.special.lpmv`` (associated Legendre
+functions) and ``scipy.linalg.expm`` (matrix exponential).
 
 Conventions (readings of the paper, each repeated in the design notes):
 
@@ -43,6 +45,8 @@ import math
 from dataclasses import dataclass
 
 import numpy as np
+import scipy.linalg
+import scipy.special
 
 PHI = (1.0 + math.sqrt(5.0)) / 2.0
 RHO_N = math.pi
@@ -495,3 +499,106 @@ def upsilon(f, bank: Bank, power=1.5):
     """Upsilon f = W^{*,ext} Phi W f = W^* P_psi Phi W f (Sec. 4.1), with the
     soft threshold Phi and the exact (clamped) reconstruction as W^{*,ext}."""
     return inverse(soft_threshold(forward(f, bank), power), bank)
+
+
+# ---------------------------------------------------------------------------
+# Linear left-invariant diffusion on R^3 x| S^2 (Sec. 4.1, the flows with a
+# constant diagonal D_ij; the adaptive choice of D_ij is not part of the paper)
+# ---------------------------------------------------------------------------
+@dataclass(frozen=True)
+class Diffusion:
+    """dW/dt = [D11 (A1^2 + A2^2) + D33 A3^2 + D44 (A4^2 + A5^2)] W. For a
+    function of (x, n) the left-invariant fields give A3 = n . grad_x,
+    A1^2 + A2^2 = Laplace_x - (n . grad_x)^2 and A4^2 + A5^2 = the
+    Laplace-Beltrami operator of S^2 in n at fixed x (D66 is irrelevant by the
+    equivalence relation of Sec. 4.1)."""
+    t: float = 10.0       # diffusion time (Fig. 5 uses t = 10)
+    steps: int = 8        # Strang steps
+    D11: float = 0.0      # spatial, perpendicular to n
+    D33: float = 1.0      # spatial, along n
+    D44: float = 0.01     # angular
+    sh_degree: int = 0    # degree of the discrete Laplace-Beltrami; 0 = the largest
+                          # l whose (l + 1)^2 harmonics are independent on the set
+
+
+def _sh_full_rank(lmax, V):
+    Y, _ = real_sh_basis(lmax, V)
+    Y = Y / np.linalg.norm(Y, axis=0)
+    s = np.linalg.svd(Y, compute_uv=False)
+    return s[-1] > 1e-6 * s[0]
+
+
+def sh_degree_for(V, sh_degree=0):
+    """The degree of the discrete Laplace-Beltrami operator: the given one, or
+    the largest l with (l + 1)^2 <= N_o whose real harmonics are linearly
+    independent on the orientation set (on the subdivided octahedra a few
+    harmonics of the top degree coincide)."""
+    if sh_degree > 0:
+        return sh_degree
+    l = 0
+    while (l + 2) ** 2 <= len(V):
+        l += 1
+    while l > 0 and not _sh_full_rank(l, V):
+        l -= 1
+    return l
+
+
+def real_sh_basis(lmax, V):
+    """Real spherical harmonics up to degree lmax at the unit vectors V
+    (unnormalised: P_l^|m|(z) cos(m phi) or sin(|m| phi)), with the degree of
+    every column."""
+    V = np.asarray(V, dtype=np.float64)
+    z = np.clip(V[:, 2], -1.0, 1.0)
+    ph = np.arctan2(V[:, 1], V[:, 0])
+    cols, deg = [], []
+    for l in range(lmax + 1):
+        for m in range(-l, l + 1):
+            P = scipy.special.lpmv(abs(m), l, z)
+            cols.append(P * (np.sin(-m * ph) if m < 0 else np.cos(m * ph)))
+            deg.append(l)
+    return np.stack(cols, axis=1), np.array(deg)
+
+
+def angular_laplacian(V, lmax):
+    """Discrete Laplace-Beltrami operator on the orientation set: fit the
+    values by real spherical harmonics up to degree lmax (pseudo-inverse,
+    as for the profile fit of Sec. 3.2), scale degree l by -l(l+1), evaluate."""
+    Y, deg = real_sh_basis(lmax, V)
+    return Y @ np.diag(-(deg * (deg + 1.0))) @ np.linalg.pinv(Y)
+
+
+def spatial_rates(bank: Bank, D: Diffusion):
+    """r_i(w) = D11 (|w|^2 - (w.n_i)^2) + D33 (w.n_i)^2: the symbol of
+    -[D11 (A1^2 + A2^2) + D33 A3^2] for orientation i, (N_o, nz, ny, nx)."""
+    wz, wy, wx = freq_grid(bank.dims)
+    r2 = wz ** 2 + wy ** 2 + wx ** 2
+    out = np.empty((bank.n_o,) + bank.dims)
+    for i, (nx, ny, nz) in enumerate(bank.orients):
+        a2 = (wx * nx + wy * ny + wz * nz) ** 2
+        out[i] = D.D11 * (r2 - a2) + D.D33 * a2
+    return out
+
+
+def diffuse(U, bank: Bank, D: Diffusion):
+    """Phi_t U for a stored score: in the Fourier domain of x, K Strang steps
+    of the spatial part exp(-dt/2 r_i) (exact per orientation), the angular
+    part exp(dt D44 L) (a matrix over the orientations) and the spatial part
+    again, dt = t / K."""
+    K = int(D.steps)
+    dt = D.t / K
+    half = np.exp(-0.5 * dt * spatial_rates(bank, D))
+    EA = scipy.linalg.expm(dt * D.D44 * angular_laplacian(bank.orients,
+                                                           sh_degree_for(bank.orients, D.sh_degree)))
+    Uh = np.stack([np.fft.fftn(U[i]) for i in range(bank.n_o)])
+    for _ in range(K):
+        Uh = half * Uh
+        Uh = np.tensordot(EA, Uh, axes=(1, 0))
+        Uh = half * Uh
+    return np.stack([np.fft.ifftn(Uh[i]) for i in range(bank.n_o)])
+
+
+def enhance_linear(f, bank: Bank, D: Diffusion):
+    """Upsilon f = W^{*,ext} Phi_t W f with the linear diffusion Phi_t
+    (Sec. 4.1): forward transform, evolution of the score, exact
+    reconstruction."""
+    return inverse(diffuse(forward(f, bank), bank, D), bank)

@@ -1,9 +1,11 @@
 """Pins of the oracle's extensions: the octahedral orientation sets, the plate
-detector profile, the approximate reconstruction, the projection P_psi and
-the soft-threshold processing Upsilon. As in test_oracle_pins.py, each test
-checks the oracle against something other than itself: a spherical design
-identity, grid rotations, the detector semantics the paper states, and
-algebraic properties (fixed points, idempotence, homogeneity)."""
+detector profile, the approximate reconstruction, the projection P_psi, the
+soft-threshold processing Upsilon and the linear left-invariant diffusion.
+As in test_oracle_pins.py, each test checks the oracle against something
+other than itself: a spherical design identity, grid rotations, the detector
+semantics the paper states, harmonic polynomials, the heat kernel, the order
+of the splitting and algebraic properties (fixed points, idempotence,
+homogeneity)."""
 import numpy as np
 import pytest
 
@@ -176,3 +178,74 @@ def test_upsilon_identities():
     assert np.abs(O.upsilon(-f, bank, 1.5) + u).max() < 1e-12 * np.abs(u).max()
     assert np.abs(O.upsilon(4.0 * f, bank, 1.5) - 8.0 * u).max() < 1e-12 * np.abs(u).max()
     assert np.abs(u - ref).max() > 0.01 * np.abs(ref).max()
+
+
+# ---------------------------------------------------------------------------
+# linear left-invariant diffusion (Sec. 4.1 with a constant diagonal D_ij)
+# ---------------------------------------------------------------------------
+def test_discrete_laplace_beltrami_on_harmonic_polynomials():
+    """Restrictions of harmonic polynomials of degree l to S^2 are
+    eigenfunctions of the Laplace-Beltrami operator with eigenvalue -l(l+1)."""
+    V = O.icosa_orientations(1)
+    L = O.angular_laplacian(V, O.sh_degree_for(V))
+    x, y, z = V.T
+    for u, ev in ((np.ones_like(z), 0), (z, -2), (x * y, -6), (z * z - 1.0 / 3.0, -6),
+                  (x * y * z, -12), (x ** 3 - 3 * x * y * y, -12)):
+        assert np.abs(L @ u - ev * u).max() < 1e-10
+    import scipy.linalg
+    E = scipy.linalg.expm(0.3 * L)
+    assert np.abs(E @ z - np.exp(-0.6) * z).max() < 1e-10
+
+
+@pytest.mark.parametrize("make,n,deg", [(O.icosa_orientations, 1, 5), (O.octa_orientations, 1, 3),
+                                        (O.octa_orientations, 2, 6), (O.icosa_orientations, 2, 11)])
+def test_laplacian_degree_choice(make, n, deg):
+    assert O.sh_degree_for(make(n)) == deg
+
+
+def test_isotropic_spatial_diffusion_is_the_heat_kernel():
+    """With D44 = 0 and D11 = D33 = D the evolution multiplies every
+    orientation by exp(-t D |w|^2), which commutes with W: the enhancement is
+    the ball-limited heat kernel, for any number of Strang steps."""
+    dims = (12, 16, 10)
+    f = np.random.default_rng(35).standard_normal(dims)
+    bank = O.Bank(dims, O.icosa_orientations(1), O.Params(L=8))
+    wz, wy, wx = O.freq_grid(dims)
+    r2 = wz ** 2 + wy ** 2 + wx ** 2
+    ref = np.fft.ifftn(np.fft.fftn(f) * (r2 < np.pi ** 2) * np.exp(-1.5 * 0.4 * r2)).real
+    for K in (1, 3):
+        g = O.enhance_linear(f, bank, O.Diffusion(t=1.5, steps=K, D11=0.4, D33=0.4, D44=0.0))
+        assert np.abs(g - ref).max() < 1e-12 * np.abs(ref).max()
+    g0 = O.enhance_linear(f, bank, O.Diffusion(t=0.0, steps=2))
+    ref0 = np.fft.ifftn(np.fft.fftn(f) * (r2 < np.pi ** 2)).real
+    assert np.abs(g0 - ref0).max() < 1e-12
+
+
+def test_angular_diffusion_keeps_orientation_constant_scores():
+    dims = (8, 8, 8)
+    bank = O.Bank(dims, O.icosa_orientations(1), O.Params(L=8))
+    g = np.random.default_rng(36).standard_normal(dims)
+    U = np.broadcast_to(g, (bank.n_o,) + dims).astype(np.complex128)
+    out = O.diffuse(U, bank, O.Diffusion(t=3.0, steps=4, D11=0.0, D33=0.0, D44=0.5))
+    assert np.abs(out - U).max() < 1e-12
+
+
+def test_strang_splitting_is_second_order():
+    dims = (12, 12, 12)
+    f = np.random.default_rng(37).standard_normal(dims)
+    bank = O.Bank(dims, O.icosa_orientations(1), O.Params(L=8))
+    D = dict(t=2.0, D11=0.1, D33=1.0, D44=0.05)
+    ref = O.enhance_linear(f, bank, O.Diffusion(steps=256, **D))
+    err = [np.abs(O.enhance_linear(f, bank, O.Diffusion(steps=K, **D)) - ref).max()
+           for K in (4, 8, 16)]
+    for a, b in zip(err[:-1], err[1:]):
+        assert 3.5 < a / b < 4.5
+
+
+def test_diffused_score_of_a_real_image_keeps_antipodal_conjugacy():
+    dims = (10, 12, 8)
+    f = np.random.default_rng(38).standard_normal(dims)
+    bank = O.Bank(dims, O.icosa_orientations(1), O.Params(L=8))
+    W = O.diffuse(O.forward(f, bank), bank, O.Diffusion(t=2.0, steps=3, D11=0.2, D33=1.0, D44=0.1))
+    h = bank.n_o // 2
+    assert np.abs(W[h:] - np.conj(W[:h])).max() < 1e-13 * np.abs(W).max()
