@@ -522,9 +522,7 @@ class Diffusion:
 
 
 def _sh_full_rank(lmax, V):
-    Y, _ = real_sh_basis(lmax, V)
-    Y = Y / np.linalg.norm(Y, axis=0)
-    s = np.linalg.svd(Y, compute_uv=False)
+    s = np.linalg.svd(real_sh_basis(lmax, V)[0], compute_uv=False)
     return s[-1] > 1e-6 * s[0]
 
 
@@ -544,17 +542,22 @@ def sh_degree_for(V, sh_degree=0):
 
 
 def real_sh_basis(lmax, V):
-    """Real spherical harmonics up to degree lmax at the unit vectors V
-    (unnormalised: P_l^|m|(z) cos(m phi) or sin(|m| phi)), with the degree of
-    every column."""
+    """Orthonormal real spherical harmonics up to degree lmax at the unit
+    vectors V: N_lm P_l^|m|(z) cos(m phi) or sin(|m| phi), with N_lm^2 =
+    (2 - delta_m0) (2l+1)/(4 pi) (l-|m|)!/(l+|m|)!; and the degree of every
+    column. (Unit norms on the sphere keep a harmonic that vanishes on the
+    set visible as a near-zero column.)"""
     V = np.asarray(V, dtype=np.float64)
     z = np.clip(V[:, 2], -1.0, 1.0)
     ph = np.arctan2(V[:, 1], V[:, 0])
     cols, deg = [], []
     for l in range(lmax + 1):
         for m in range(-l, l + 1):
-            P = scipy.special.lpmv(abs(m), l, z)
-            cols.append(P * (np.sin(-m * ph) if m < 0 else np.cos(m * ph)))
+            am = abs(m)
+            nrm = math.sqrt((2.0 - (m == 0)) * (2 * l + 1) / (4.0 * math.pi)
+                            * math.factorial(l - am) / math.factorial(l + am))
+            P = scipy.special.lpmv(am, l, z)
+            cols.append(nrm * P * (np.sin(am * ph) if m < 0 else np.cos(am * ph)))
             deg.append(l)
     return np.stack(cols, axis=1), np.array(deg)
 
