@@ -185,6 +185,51 @@ os3d_status os3d_soft_threshold(const void* in, void* out, os3d_udtype udtype, l
 os3d_status os3d_upsilon(const os3d_bank* bank, const float* f, int batch, float* f_out,
                          double power, void* workspace, void* stream);
 
+/* Linear left-invariant diffusion on R^3 x| S^2 (Sec. 4.1 with a constant
+ * diagonal D_ij): dW/dt = [D11 (A1^2 + A2^2) + D33 A3^2 + D44 (A4^2 + A5^2)] W,
+ * where for a function of (x, n) A3 = n . grad_x, A1^2 + A2^2 =
+ * Laplace_x - (n . grad_x)^2 and A4^2 + A5^2 is the Laplace-Beltrami
+ * operator of S^2 in n (D66 drops out by the equivalence relation). */
+typedef struct {
+  double t;         /* diffusion time >= 0 (Fig. 5: t = 10)                          */
+  int steps;        /* Strang splitting steps K, 1..4096                             */
+  double D11;       /* spatial diffusion perpendicular to n, >= 0                    */
+  double D33;       /* spatial diffusion along n, >= 0                               */
+  double D44;       /* angular diffusion, >= 0                                       */
+  int sh_degree;    /* degree of the discrete Laplace-Beltrami operator, 0..15; 0 = the
+                       largest l with (l+1)^2 <= N_o whose real spherical harmonics are
+                       linearly independent on the orientation set                  */
+} os3d_diffusion;
+
+/* t = 10, steps = 8, D11 = 0, D33 = 1, D44 = 0.01, sh_degree = 0. Host only. */
+os3d_status os3d_default_diffusion(os3d_diffusion* d);
+
+/* The angular propagator exp(tau L) of the discrete Laplace-Beltrami operator
+ * on n orientations `orient` (host, n x 3) into E (host, n x n doubles,
+ * row-major), in FP64: E = I + Y (exp(tau Lambda) - I) (Y^T Y)^-1 Y^T with
+ * the real spherical harmonics Y up to degree `sh_degree` (0 = automatic, as
+ * in os3d_diffusion). *degree_used (may be NULL) receives the degree. Host
+ * only. Errors: EINVAL (NULL, n < 1, tau < 0, dependent harmonics). */
+os3d_status os3d_angular_propagator(const double* orient, int n, int sh_degree, double tau,
+                                    double* E, int* degree_used);
+
+/* Enhancement Upsilon f = W^{*,ext} Phi_t W f with the linear diffusion Phi_t
+ * (Sec. 4.1), for `batch` real volumes f into f_out (device, float). The
+ * evolution is integrated in the Fourier domain of x: per orientation the
+ * spatial generators are the exact factor exp(-dt r_i(w)), r_i(w) = D11 (|w|^2
+ * - (w.n_i)^2) + D33 (w.n_i)^2; the angular generator is the discrete
+ * Laplace-Beltrami operator L = Y diag(-l(l+1)) Y^+ of the real spherical
+ * harmonics Y on the orientation set, applied as exp(dt D44 L) (FP64 on the
+ * host); K Strang steps of dt = t/K (half spatial, angular, half spatial).
+ * Because every operator in the cascade commutes with translations, the
+ * whole of W^{*,ext} Phi_t W acts on f_hat through one real factor per
+ * frequency, which one GPU thread per frequency integrates: the score is never
+ * formed and no per-orientation transform runs. Orientation sets of at most 68
+ * vectors (EUNSUPPORTED above). Errors: EINVAL (NULL, parameters out of
+ * range, dependent harmonics at the requested degree), EUNSUPPORTED, ECUDA. */
+os3d_status os3d_enhance_linear(const os3d_bank* bank, const float* f, int batch, float* f_out,
+                                const os3d_diffusion* d, void* workspace, void* stream);
+
 /* Sizes: workspace bytes one call needs, and device bytes of one volume's
  * score (N_o x nz x ny x nx x 8). Host only. */
 os3d_status os3d_bank_info(const os3d_bank* bank, size_t* workspace_bytes,
@@ -282,7 +327,8 @@ enum {
   OS3D_KIND_XY_SOFT = 8,       /* Upsilon: IDFT_xy, soft threshold, DFT_xy     */
   OS3D_KIND_APPROX = 9,        /* approximate reconstruction: orientation sum  */
   OS3D_KIND_SOFT = 10,         /* soft threshold of a stored score             */
-  OS3D_KIND_COUNT = 11
+  OS3D_KIND_ENHANCE = 11,      /* linear diffusion: per-frequency integration  */
+  OS3D_KIND_COUNT = 12
 };
 
 /* Number of kernels this library has launched in this process. Host only. */

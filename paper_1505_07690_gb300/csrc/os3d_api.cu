@@ -1047,6 +1047,77 @@ os3d_status os3d_soft_threshold(const void* in, void* out, os3d_udtype udtype, l
   return OS3D_OK;
 }
 
+os3d_status os3d_default_diffusion(os3d_diffusion* d) {
+  if (!d) return OS3D_EINVAL;
+  d->t = 10.0;
+  d->steps = 8;
+  d->D11 = 0.0;
+  d->D33 = 1.0;
+  d->D44 = 0.01;
+  d->sh_degree = 0;
+  return OS3D_OK;
+}
+
+os3d_status os3d_angular_propagator(const double* orient, int n, int sh_degree, double tau,
+                                    double* E, int* degree_used) {
+  if (!orient || !E || n < 1 || !(tau >= 0.0) || !std::isfinite(tau) || sh_degree < 0 ||
+      sh_degree > 15)
+    return OS3D_EINVAL;
+  std::vector<double> e;
+  const int l = angular_propagator(orient, n, sh_degree, tau, e);
+  if (l < 0) return OS3D_EINVAL;
+  std::copy(e.begin(), e.end(), E);
+  if (degree_used) *degree_used = l;
+  return OS3D_OK;
+}
+
+os3d_status os3d_enhance_linear(const os3d_bank* b, const float* f, int batch, float* f_out,
+                                const os3d_diffusion* d, void* ws, void* stream) {
+  const os3d_status st = check_call(b, f, f_out, batch, OS3D_U_C64, ws);
+  if (st != OS3D_OK) return st;
+  if (!d) return OS3D_EINVAL;
+  auto ok = [](double x) { return std::isfinite(x) && x >= 0.0; };
+  if (!ok(d->t) || !ok(d->D11) || !ok(d->D33) || !ok(d->D44) || d->steps < 1 ||
+      d->steps > 4096 || d->sh_degree < 0 || d->sh_degree > 15)
+    return OS3D_EINVAL;
+  if (b->n_o > kMaxOrientE) return OS3D_EUNSUPPORTED;
+  const double dt = d->t / d->steps;
+  std::vector<double> E;
+  if (angular_propagator(b->orient.data(), b->n_o, d->sh_degree, dt * d->D44, E) < 0)
+    return OS3D_EINVAL;
+  static thread_local EnhanceArgs e;   // ~20 KB: kept off the stack
+  e = EnhanceArgs{};
+  e.nz = b->dims[0];
+  e.ny = b->dims[1];
+  e.nx = b->dims[2];
+  e.wz = float(2.0 * kPi / b->dims[0]);
+  e.wy = float(2.0 * kPi / b->dims[1]);
+  e.wx = float(2.0 * kPi / b->dims[2]);
+  e.n3 = float(b->nvox);
+  e.n_o = b->n_o;
+  e.steps = d->steps;
+  e.half_dt = float(0.5 * dt);
+  e.D11 = float(d->D11);
+  e.D33 = float(d->D33);
+  for (int i = 0; i < b->n_o; ++i) {
+    for (int q = 0; q < 3; ++q) e.nvec[i][q] = float(b->orient[3 * i + q]);
+    for (int j = 0; j < b->n_o; ++j) e.E[i * kMaxOrientE + j] = float(E[(size_t)i * b->n_o + j]);
+  }
+  e.h = b->h;
+  cudaStream_t s = (cudaStream_t)stream;
+  const Work w = carve(b, ws);
+  e.fh = w.fh;
+  e.A = w.A[0];
+  for (int v = 0; v < batch; ++v) {
+    os3d_status r = prep_fhat(b, f, v, w, s);
+    if (r != OS3D_OK) return r;
+    OS3D_CK(counted_launch(OS3D_KIND_ENHANCE, s, [&] { return launch_enhance(e, b->ev, s); }));
+    r = finish_real(b, w, 1, b->GM, f_out, v, s);
+    if (r != OS3D_OK) return r;
+  }
+  return OS3D_OK;
+}
+
 os3d_status os3d_upsilon(const os3d_bank* b, const float* f, int batch, float* f_out,
                          double power, void* ws, void* stream) {
   const os3d_status st = check_call(b, f, f_out, batch, OS3D_U_C64, ws);
@@ -1197,7 +1268,7 @@ os3d_status os3d_profile_reset(void) {
 const char* os3d_kernel_kind_name(int kind) {
   static const char* names[OS3D_KIND_COUNT] = {
       "xy_fwd_real", "xy_fwd_score", "xy_inv_score", "xy_inv_real", "z_fwd_prep", "z_fwd_score",
-      "z_inv_score", "z_inv_final", "xy_soft", "approx_sum", "soft_threshold"};
+      "z_inv_score", "z_inv_final", "xy_soft", "approx_sum", "soft_threshold", "enhance_linear"};
   return (kind >= 0 && kind < OS3D_KIND_COUNT) ? names[kind] : "unknown";
 }
 

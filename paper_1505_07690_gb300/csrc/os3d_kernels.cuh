@@ -3,6 +3,7 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <cstdint>
+#include <vector>
 
 namespace os3d {
 
@@ -96,6 +97,28 @@ cudaError_t launch_soft_scores(const void* in, void* out, int ubf16, long long c
 // in place on a.nslots volumes of a.out, a.slot_stride apart, nvox each;
 // slot s scaled by 2 when a.ub[s] >= 0 (an antipodal pair)
 cudaError_t launch_soft_slots(const PassArgs& a, long long nvox, cudaStream_t s);
+
+// Linear left-invariant diffusion (os3d_diffusion.cu): per-frequency
+// integration of the orientation vector; orientation sets up to 68.
+constexpr int kMaxOrientE = 68;
+struct EnhanceArgs {
+  const float2* fh;           // f_hat G / n^3
+  float2* A;                  // out: fh * n^3 h^T E h (then x G/(n^3 max(M,eps)), IDFT)
+  int nz, ny, nx;
+  float wz, wy, wx;           // 2 pi / n per axis
+  float n3;                   // nz ny nx
+  int n_o;
+  int steps;                  // Strang steps K
+  float half_dt;              // t / (2K)
+  float D11, D33;
+  float nvec[kMaxOrientE][3];
+  float E[kMaxOrientE * kMaxOrientE];   // exp(dt D44 L), row-major, row stride kMaxOrientE
+  HEval h;
+};
+cudaError_t launch_enhance(const EnhanceArgs& a, int ev, cudaStream_t s);
+// host: exp(tau L) of the discrete Laplace-Beltrami operator (n x n, FP64);
+// returns the spherical-harmonic degree used, or -1
+int angular_propagator(const double* V, int n, int sh_degree, double tau, std::vector<double>& E);
 
 // FP64 bank kernels
 cudaError_t launch_fit(const double* d_z, const double* d_w, int npts, int mode, int k,

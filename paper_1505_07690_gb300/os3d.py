@@ -28,6 +28,11 @@ class os3d_params(ctypes.Structure):
                 ("overlap", ctypes.c_int), ("profile", ctypes.c_int)]
 
 
+class os3d_diffusion(ctypes.Structure):
+    _fields_ = [("t", ctypes.c_double), ("steps", ctypes.c_int), ("D11", ctypes.c_double),
+                ("D33", ctypes.c_double), ("D44", ctypes.c_double), ("sh_degree", ctypes.c_int)]
+
+
 class os3d_server_config(ctypes.Structure):
     _fields_ = [("arena_bytes", ctypes.c_size_t), ("max_inflight", ctypes.c_int),
                 ("udtype", ctypes.c_int)]
@@ -60,6 +65,10 @@ def lib():
         L.os3d_project.argtypes = [vp, vp, i, i, vp, vp, vp]
         L.os3d_soft_threshold.argtypes = [vp, vp, i, ctypes.c_longlong, d, vp]
         L.os3d_upsilon.argtypes = [vp, vp, i, vp, d, vp, vp]
+        L.os3d_default_diffusion.argtypes = [ctypes.POINTER(os3d_diffusion)]
+        L.os3d_angular_propagator.argtypes = [ctypes.POINTER(d), i, i, d, ctypes.POINTER(d),
+                                              ctypes.POINTER(i)]
+        L.os3d_enhance_linear.argtypes = [vp, vp, i, vp, ctypes.POINTER(os3d_diffusion), vp, vp]
         L.os3d_make_wavelets.argtypes = [ctypes.POINTER(i), ctypes.POINTER(d), i,
                                          ctypes.POINTER(os3d_params), vp, ctypes.POINTER(vp)]
         L.os3d_forward.argtypes = [vp, vp, i, vp, i, vp, vp]
@@ -93,7 +102,8 @@ def lib():
                      "os3d_server_create", "os3d_server_submit", "os3d_server_wait",
                      "os3d_server_destroy", "os3d_octa_orientations",
                      "os3d_approx_reconstruct", "os3d_project", "os3d_soft_threshold",
-                     "os3d_upsilon"):
+                     "os3d_upsilon", "os3d_default_diffusion", "os3d_enhance_linear",
+                     "os3d_angular_propagator"):
             getattr(L, name).restype = i
         _lib = L
     return _lib
@@ -354,7 +364,48 @@ def os3d_upsilon(bank: Bank, f, power: float = 1.5, f_out=None, workspace=None, 
     return f_out
 
 
-OS3D_KIND_COUNT = 11
+def os3d_default_diffusion(**overrides) -> os3d_diffusion:
+    d = os3d_diffusion()
+    _check(lib().os3d_default_diffusion(ctypes.byref(d)), "os3d_default_diffusion")
+    for k, v in overrides.items():
+        setattr(d, k, v)
+    return d
+
+
+def os3d_angular_propagator(orient, tau: float, sh_degree: int = 0):
+    """(exp(tau L) as an (n, n) array, degree used) for the discrete
+    Laplace-Beltrami operator on the orientation set (host, FP64)."""
+    o = np.ascontiguousarray(np.asarray(orient, dtype=np.float64).reshape(-1, 3))
+    n = len(o)
+    E = np.zeros((n, n))
+    deg = ctypes.c_int(0)
+    dp = ctypes.POINTER(ctypes.c_double)
+    _check(lib().os3d_angular_propagator(o.ctypes.data_as(dp), n, int(sh_degree), float(tau),
+                                         E.ctypes.data_as(dp), ctypes.byref(deg)),
+           "os3d_angular_propagator")
+    return E, deg.value
+
+
+def os3d_enhance_linear(bank: Bank, f, diffusion: os3d_diffusion | None = None, f_out=None,
+                        workspace=None, stream=None):
+    """Upsilon f = W^{*,ext} Phi_t W f with the linear left-invariant diffusion
+    Phi_t (Sec. 4.1), integrated per frequency without forming the score."""
+    import torch
+    if not (f.is_cuda and f.dtype == torch.float32 and f.is_contiguous()):
+        raise ValueError("f must be a contiguous float32 CUDA tensor")
+    batch = _batch_of(f, 3, bank.dims)
+    d = diffusion if diffusion is not None else os3d_default_diffusion()
+    if f_out is None:
+        f_out = torch.empty_like(f)
+    if not (f_out.is_cuda and f_out.dtype == torch.float32 and f_out.is_contiguous()
+            and f_out.numel() == f.numel()):
+        raise ValueError("f_out must be a contiguous float32 CUDA tensor like f")
+    _check(lib().os3d_enhance_linear(bank.handle, _ptr(f), batch, _ptr(f_out), ctypes.byref(d),
+                                     _ws_ptr(workspace), _stream(stream)), "os3d_enhance_linear")
+    return f_out
+
+
+OS3D_KIND_COUNT = 12
 
 
 def os3d_launch_count() -> int:

@@ -48,6 +48,25 @@ def test_octahedral_orientations_match_oracle(L):
     assert L.os3d_octa_orientations(6, None, 0, ctypes.byref(n)) == 1
 
 
+@pytest.mark.parametrize("make,sub", [(O.icosa_orientations, 0), (O.icosa_orientations, 1),
+                                      (O.octa_orientations, 1), (O.octa_orientations, 2),
+                                      (O.octa_orientations, 0)])
+def test_angular_propagator_matches_oracle(L, make, sub):
+    """Host FP64 closed form exp(tau L) = I + Y (e^{tau Lambda} - I) Y^+ against
+    the oracle's matrix exponential of its Laplace-Beltrami matrix."""
+    import scipy.linalg
+    from paper_1505_07690_gb300 import os3d
+    V = make(sub)
+    for tau in (0.0, 0.05, 0.7):
+        E, deg = os3d.os3d_angular_propagator(V, tau)
+        assert deg == O.sh_degree_for(V)
+        ref = scipy.linalg.expm(tau * O.angular_laplacian(V, deg))
+        assert np.abs(E - ref).max() < 1e-10
+    E, deg = os3d.os3d_angular_propagator(V, 0.3, sh_degree=1)
+    assert deg == 1
+    assert np.abs(E - scipy.linalg.expm(0.3 * O.angular_laplacian(V, 1))).max() < 1e-10
+
+
 def test_orientation_capacity_and_range(L):
     n = ctypes.c_int(0)
     buf = (ctypes.c_double * 30)()
@@ -107,6 +126,17 @@ def test_argument_errors_before_any_launch(L):
         assert L.os3d_soft_threshold(a16, a16, 0, 4, pw, None) == 1
     assert L.os3d_soft_threshold(a16, a16, 2, 4, 1.5, None) == 1       # unknown udtype
     assert L.os3d_soft_threshold(a16, a16, 0, 0, 1.5, None) == 0       # nothing to do
+    d = os3d.os3d_default_diffusion()
+    assert (d.t, d.steps, d.D11, d.D33, d.D44, d.sh_degree) == (10.0, 8, 0.0, 1.0, 0.01, 0)
+    assert L.os3d_enhance_linear(None, None, 1, None, ctypes.byref(d), None, None) == 1
+    E = (ctypes.c_double * 36)()
+    Vp6 = O.octa_orientations(0)
+    assert L.os3d_angular_propagator(None, 6, 0, 0.1, E, None) == 1
+    assert L.os3d_angular_propagator(Vp6.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), 6, 0,
+                                     -0.1, E, None) == 1
+    # degree 2 needs 9 independent harmonics: impossible on 6 points
+    assert L.os3d_angular_propagator(Vp6.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), 6, 2,
+                                     0.1, E, None) == 1
 
 
 def test_injected_allocation_failure(L, monkeypatch):
