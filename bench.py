@@ -350,6 +350,7 @@ def run_ours(args):
         return a.elapsed_time(b) / n
 
     hbm = peaks["hbm_gbs"]
+    nsm = torch.cuda.get_device_properties(local).multi_processor_count
     ops = {}
     ms_a = timed(lambda: os3d.os3d_approx_reconstruct(bank, U, frec), args.steps)
     by_a = n_o * nvox * esize + nvox * 4
@@ -365,6 +366,33 @@ def run_ours(args):
     ms_u = timed(lambda: os3d.os3d_upsilon(bank, f, 1.5, fu), args.steps)
     ops["upsilon_fused"] = {"ms": ms_u, "value": nvox * n_o / (ms_u / 1e3), "unit": UNIT,
                             "score_bytes_stored": 0}
+    # linear diffusion: 42 orientations (the flows of Sec. 4.1 use N_o = 42), same grid
+    V42 = os3d.os3d_icosa_orientations(1)
+    bank42 = os3d.os3d_make_wavelets(dims, V42, os3d.os3d_default_params(L=w["L"]))
+    dif = os3d.os3d_default_diffusion()
+    os3d.os3d_profile_reset()
+    os3d.os3d_profile_enable(True)
+    ms_e = timed(lambda: os3d.os3d_enhance_linear(bank42, f, dif, fu), args.steps)
+    torch.cuda.synchronize()
+    os3d.os3d_profile_enable(False)
+    pe = os3d.os3d_profile_read()["enhance_linear"]
+    # algorithmic FP32 flops per in-ball frequency: K steps of an N_o x N_o
+    # matrix-vector product (2 N_o^2) plus 2 N_o wavelet evaluations (Horner,
+    # 2 x 17 flops each) and the spatial factors
+    wz = np.fft.fftfreq(dims[0])[:, None, None] * 2 * np.pi
+    wy = np.fft.fftfreq(dims[1])[None, :, None] * 2 * np.pi
+    wx = np.fft.fftfreq(dims[2])[None, None, :] * 2 * np.pi
+    inball = int(np.count_nonzero(wz ** 2 + wy ** 2 + wx ** 2 < np.pi ** 2))
+    no42 = len(V42)
+    flops = inball * (dif.steps * 2 * no42 * no42 + 2 * no42 * 34 + no42 * 12)
+    k_ms = pe[1] / max(pe[0], 1)
+    fp32_peak = nsm * 128 * 2 * (clk["sm_mhz"] if clk else 2070.0) * 1e6 / 1e12
+    ops["enhance_linear"] = {
+        "ms": ms_e, "n_o": no42, "steps": dif.steps,
+        "value": nvox * no42 / (ms_e / 1e3), "unit": UNIT,
+        "kernel_ms": k_ms, "kernel_tflops": flops / (k_ms / 1e3) / 1e12,
+        "fp32_peak_tflops": fp32_peak,
+        "frac_fp32": flops / (k_ms / 1e3) / 1e12 / fp32_peak}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -1,7 +1,7 @@
 """GPU parity of the extensions through the C ABI against the FP64 oracle:
 the plate-detector profile, the octahedral orientation sets, the approximate
-reconstruction, the projection P_psi, the soft threshold and the fused
-Upsilon = W^{*,ext} Phi W. Tolerances as in test_gpu_parity.py: relative L2
+reconstruction, the projection P_psi, the soft threshold, the fused
+Upsilon = W^{*,ext} Phi W and the linear left-invariant diffusion. Tolerances as in test_gpu_parity.py: relative L2
 error <= 1e-5 for FP32 results, 5e-3 where a score is stored in BF16."""
 import numpy as np
 import pytest
@@ -206,3 +206,52 @@ def test_upsilon_headline_size_properties(M):
     u = _np(M.os3d_upsilon(bank, fd, 1.5))
     assert rel(_np(M.os3d_upsilon(bank, 4.0 * fd, 1.5)), 8.0 * u) <= TOL
     assert rel(_np(M.os3d_upsilon(bank, -fd, 1.5)), -u) <= TOL
+
+
+# ---------------------------------------------------------------------------
+# linear left-invariant diffusion (Sec. 4.1)
+# ---------------------------------------------------------------------------
+def _diff(M, **kw):
+    d = M.os3d_default_diffusion(**kw)
+    return d, O.Diffusion(t=d.t, steps=d.steps, D11=d.D11, D33=d.D33, D44=d.D44,
+                          sh_degree=d.sh_degree)
+
+
+@pytest.mark.parametrize("make,sub,dims,kw", [
+    (O.icosa_orientations, 1, (32, 32, 32), {}),
+    (O.icosa_orientations, 1, (32, 32, 32), dict(t=2.0, steps=3, D11=0.2, D33=1.0, D44=0.1)),
+    (O.octa_orientations, 1, (32, 32, 32), dict(t=4.0, steps=5, D11=0.05, D33=0.5, D44=0.2)),
+    (O.icosa_orientations, 0, (16, 16, 16), dict(D44=0.3)),
+    (O.octa_orientations, 2, (16, 16, 16), dict(t=3.0, steps=4, D44=0.05)),
+    (O.icosa_orientations, 1, (32, 48, 64), dict(t=5.0, steps=6, D11=0.1)),
+])
+def test_enhance_linear_against_oracle(M, make, sub, dims, kw):
+    V = make(sub)
+    bank, ob = _pair(M, dims, V, L=12)
+    d, od = _diff(M, **kw)
+    f = synth.straight_tubes(dims, 3, seed=40, noise=0.1)
+    g = _np(M.os3d_enhance_linear(bank, _cuda(f), d))
+    assert rel(g, O.enhance_linear(f, ob, od)) <= TOL
+
+
+def test_enhance_linear_batch_and_identity(M):
+    dims = (32, 32, 32)
+    bank, ob = _pair(M, dims, O.icosa_orientations(1), L=12)
+    f = np.stack([synth.straight_tubes(dims, 3, seed=s) for s in (41, 42)])
+    d, od = _diff(M, t=3.0, steps=4, D11=0.1, D44=0.05)
+    g = _np(M.os3d_enhance_linear(bank, _cuda(f), d))
+    for v in range(2):
+        assert rel(g[v], O.enhance_linear(f[v], ob, od)) <= TOL
+    # t = 0: the ball projection IDFT[1_ball f_hat]
+    d0, _ = _diff(M, t=0.0, steps=1)
+    wz, wy, wx = O.freq_grid(dims)
+    ball = np.sqrt(wz ** 2 + wy ** 2 + wx ** 2) < np.pi
+    fb = np.fft.ifftn(np.fft.fftn(f[0]) * ball).real
+    assert rel(_np(M.os3d_enhance_linear(bank, _cuda(f[0]), d0)), fb) <= TOL
+
+
+def test_enhance_linear_rejects_large_orientation_sets(M):
+    bank, _ = _pair(M, (16, 16, 16), O.icosa_orientations(2), L=8)
+    with pytest.raises(M.OS3DError) as e:
+        M.os3d_enhance_linear(bank, _cuda(np.zeros((16, 16, 16), np.float32)))
+    assert e.value.status == 5
