@@ -99,6 +99,9 @@ struct os3d_bank {
   float* Gs = nullptr;                 // G / n^3
   float* GM = nullptr;                 // G / (n^3 max(M, eps))
   float* Minv = nullptr;               // 1 / max(M, eps), 0 outside the ball
+  int4* seg = nullptr;                 // frequencies inside the ball, as row segments
+  int nseg = 0, n_in = 0;              // (half of them when every orientation is paired)
+  int mirror = 0;
   void* ws = nullptr;                  // default workspace
   cudaStream_t side[2] = {nullptr, nullptr};   // consecutive blocks alternate between these
   cudaEvent_t ev_fork = nullptr, ev_join[2] = {nullptr, nullptr};
@@ -526,6 +529,22 @@ os3d_status os3d_make_wavelets(const int dims[3], const double* orient, int n_o,
     cudaGetLastError();
     return fail(OS3D_ENOMEM);
   }
+  {
+    bool all_paired = true;
+    for (int q : b->slot_b) all_paired = all_paired && q >= 0;
+    b->mirror = all_paired ? 1 : 0;
+    const std::vector<int4> sg = ball_segments(nz, ny, nx, all_paired, &b->n_in);
+    b->nseg = (int)sg.size();
+    if (b->nseg > 0) {
+      if (cudaMalloc(&b->seg, sizeof(int4) * sg.size()) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(OS3D_ENOMEM);
+      }
+      if (cudaMemcpy(b->seg, sg.data(), sizeof(int4) * sg.size(), cudaMemcpyHostToDevice) !=
+          cudaSuccess)
+        return fail(OS3D_ECUDA);
+    }
+  }
   for (int i = 0; i < 2; ++i)
     if (cudaStreamCreateWithFlags(&b->side[i], cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&b->ev_join[i], cudaEventDisableTiming) != cudaSuccess)
@@ -656,6 +675,7 @@ os3d_status os3d_destroy_bank(os3d_bank* b) {
   if (b->Gs) cudaFree(b->Gs);
   if (b->GM) cudaFree(b->GM);
   if (b->Minv) cudaFree(b->Minv);
+  if (b->seg) cudaFree(b->seg);
   if (b->ws) cudaFree(b->ws);
   for (int i = 0; i < 2; ++i) {
     if (b->side[i]) cudaStreamDestroy(b->side[i]);
@@ -1108,10 +1128,16 @@ os3d_status os3d_enhance_linear(const os3d_bank* b, const float* f, int batch, f
   const Work w = carve(b, ws);
   e.fh = w.fh;
   e.A = w.A[0];
+  e.seg = b->seg;
+  e.nseg = b->nseg;
+  e.n_in = b->n_in;
+  e.mirror = b->mirror;
   for (int v = 0; v < batch; ++v) {
     os3d_status r = prep_fhat(b, f, v, w, s);
     if (r != OS3D_OK) return r;
-    OS3D_CK(counted_launch(OS3D_KIND_ENHANCE, s, [&] { return launch_enhance(e, b->ev, s); }));
+    OS3D_CK(cudaMemsetAsync(w.A[0], 0, sizeof(float2) * b->nvox, s));
+    if (b->n_in > 0)
+      OS3D_CK(counted_launch(OS3D_KIND_ENHANCE, s, [&] { return launch_enhance(e, b->ev, s); }));
     r = finish_real(b, w, 1, b->GM, f_out, v, s);
     if (r != OS3D_OK) return r;
   }

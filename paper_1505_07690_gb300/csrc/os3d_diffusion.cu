@@ -26,85 +26,159 @@ namespace {
 constexpr int kEThreads = 128;
 constexpr double kPiH = 3.141592653589793238462643383279502884;
 
-// One thread per frequency voxel; NP = padded orientation count (multiple of 4).
+// One CTA per tile of TV = 128 listed frequencies, 4 NP threads; NP = the
+// orientation count padded to a multiple of 4. Per Strang step each thread
+// accumulates a 4 (orientations) x 8 (frequencies) tile of E V from shared
+// memory, so every propagator value it loads feeds 8 FMAs. Vectors are stored
+// [orientation][frequency] with the 8-frequency groups XOR-swizzled by the
+// orientation quad to spread the tile writes over the banks.
+constexpr int kTV = 128;
+
 template <int NP>
 constexpr size_t enhance_smem() {
-  return sizeof(float) * ((size_t)NP * NP + (size_t)NP * kEThreads + 3 * NP);
+  return sizeof(float) * ((size_t)NP * NP + 3 * (size_t)NP * kTV + 3 * NP + 5 * kTV) +
+         sizeof(int) * 2 * kTV;
+}
+
+__device__ __forceinline__ int swz(int i, int q) {
+  return ((((q >> 3) ^ (i >> 2)) & 15) << 3) | (q & 7);
 }
 
 template <int NP, int EV>
-__global__ void __launch_bounds__(kEThreads)
+__global__ void __launch_bounds__(4 * NP)
 enhance_kernel(const __grid_constant__ EnhanceArgs a) {
+  constexpr int NT = 4 * NP, TV = kTV, NQ = NP / 4;
   extern __shared__ __align__(16) float esm[];
-  float* Et = esm;                                   // Et[j * NP + i] = E[i][j]
-  float (*col)[kEThreads] = reinterpret_cast<float (*)[kEThreads]>(esm + NP * NP);
-  float (*nv)[3] = reinterpret_cast<float (*)[3]>(esm + NP * NP + NP * kEThreads);
+  float* Et = esm;                       // Et[j * NP + i] = E[i][j]
+  float* Va = Et + NP * NP;              // [i][q], two buffers
+  float* Vb = Va + NP * TV;
+  float* F = Vb + NP * TV;               // half-step factors exp(-dt/2 r_i)
+  float* nv = F + NP * TV;               // orientations (3 per row)
+  float* geo = nv + 3 * NP;              // wx, wy, wz, 1/|w|, |w|^2 per slot
+  int* vox = reinterpret_cast<int*>(geo + 5 * TV);
+  int* mvox = vox + TV;
   const int t = threadIdx.x;
-  for (int q = t; q < NP * NP; q += kEThreads) {
+  const int ig = t % NQ, vg = t / NQ;
+
+  for (int q = t; q < NP * NP; q += NT) {
     const int j = q / NP, i = q % NP;
     Et[q] = (i < a.n_o && j < a.n_o) ? a.E[i * kMaxOrientE + j] : 0.f;
   }
-  for (int q = t; q < NP * 3; q += kEThreads)
-    nv[q / 3][q % 3] = (q / 3 < a.n_o) ? a.nvec[q / 3][q % 3] : 0.f;
-  __syncthreads();
+  for (int q = t; q < 3 * NP; q += NT) nv[q] = (q / 3 < a.n_o) ? a.nvec[q / 3][q % 3] : 0.f;
 
-  const long long nvox = (long long)a.nz * a.ny * a.nx;
-  const float pi2 = 9.869604401089358f;
-  for (long long v = (long long)blockIdx.x * kEThreads + t; v < nvox;
-       v += (long long)gridDim.x * kEThreads) {
-    const int ix = int(v % a.nx), iy = int((v / a.nx) % a.ny), iz = int(v / ((long long)a.nx * a.ny));
-    const float wx = float(ix >= (a.nx + 1) / 2 ? ix - a.nx : ix) * a.wx;
-    const float wy = float(iy >= (a.ny + 1) / 2 ? iy - a.ny : iy) * a.wy;
-    const float wz = float(iz >= (a.nz + 1) / 2 ? iz - a.nz : iz) * a.wz;
-    const float r2 = fmaf(wx, wx, fmaf(wy, wy, wz * wz));
-    if (r2 >= pi2) {
-      a.A[v] = make_float2(0.f, 0.f);
-      continue;
-    }
-    const float ri = r2 > 0.f ? rsqrtf(r2) : 0.f;
-    float F[NP];
-#pragma unroll
-    for (int i = 0; i < NP; ++i) {
-      const float tau = fmaf(wx, nv[i][0], fmaf(wy, nv[i][1], wz * nv[i][2]));
-      const float rate = fmaf(a.D11, r2 - tau * tau, a.D33 * tau * tau);
-      F[i] = expf(-a.half_dt * rate);
-      float hv = 0.f;
-      if (i < a.n_o) hv = r2 > 0.f ? eval_h<EV>(a.h, tau * ri) : a.h.c0;
-      col[i][t] = hv * F[i];
-    }
-    for (int s = 0; s < a.steps; ++s) {
-      float acc[NP];
-#pragma unroll
-      for (int i = 0; i < NP; ++i) acc[i] = 0.f;
-#pragma unroll 2
-      for (int j = 0; j < NP; ++j) {
-        const float vj = col[j][t];
-        const float4* row = reinterpret_cast<const float4*>(Et + j * NP);
-#pragma unroll
-        for (int i4 = 0; i4 < NP / 4; ++i4) {
-          const float4 e = row[i4];
-          acc[4 * i4 + 0] = fmaf(e.x, vj, acc[4 * i4 + 0]);
-          acc[4 * i4 + 1] = fmaf(e.y, vj, acc[4 * i4 + 1]);
-          acc[4 * i4 + 2] = fmaf(e.z, vj, acc[4 * i4 + 2]);
-          acc[4 * i4 + 3] = fmaf(e.w, vj, acc[4 * i4 + 3]);
+  const int ntiles = (a.n_in + TV - 1) / TV;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    __syncthreads();   // previous tile done with the slot data
+    // ---- slots: frequency of every listed index of the tile
+    for (int q = t; q < TV; q += NT) {
+      const int g = tile * TV + q;
+      vox[q] = -1;
+      mvox[q] = -1;
+      if (g < a.n_in) {
+        int lo = 0, hi = a.nseg - 1;   // last segment with first index <= g
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (a.seg[mid].w <= g) lo = mid;
+          else hi = mid - 1;
         }
+        const int4 sg = a.seg[lo];
+        const int kx = sg.z + (g - sg.w);
+        const int z = sg.x, y = sg.y, x = kx < 0 ? kx + a.nx : kx;
+        vox[q] = (z * a.ny + y) * a.nx + x;
+        if (a.mirror) {
+          const int mz = z ? a.nz - z : 0, my = y ? a.ny - y : 0, mx = x ? a.nx - x : 0;
+          const int m = (mz * a.ny + my) * a.nx + mx;
+          if (m != vox[q]) mvox[q] = m;
+        }
+        const float wz = float(z >= (a.nz + 1) / 2 ? z - a.nz : z) * a.wz;
+        const float wy = float(y >= (a.ny + 1) / 2 ? y - a.ny : y) * a.wy;
+        const float wx = float(kx) * a.wx;
+        const float r2 = fmaf(wx, wx, fmaf(wy, wy, wz * wz));
+        geo[q] = wx;
+        geo[TV + q] = wy;
+        geo[2 * TV + q] = wz;
+        geo[3 * TV + q] = r2 > 0.f ? rsqrtf(r2) : 0.f;
+        geo[4 * TV + q] = r2;
+      }
+    }
+    __syncthreads();
+    // ---- F and the initial vector h F
+    for (int p = t; p < NP * TV; p += NT) {
+      const int i = p / TV, q = p % TV;
+      float f = 1.f, hv = 0.f;
+      if (vox[q] >= 0) {
+        const float tau = fmaf(geo[q], nv[3 * i], fmaf(geo[TV + q], nv[3 * i + 1], geo[2 * TV + q] * nv[3 * i + 2]));
+        const float r2 = geo[4 * TV + q];
+        f = expf(-a.half_dt * fmaf(a.D11, r2 - tau * tau, a.D33 * tau * tau));
+        if (i < a.n_o) hv = r2 > 0.f ? eval_h<EV>(a.h, tau * geo[3 * TV + q]) : a.h.c0;
+      }
+      F[i * TV + swz(i, q)] = f;
+      Va[i * TV + swz(i, q)] = hv * f;
+    }
+    __syncthreads();
+    // ---- K Strang steps: V <- F^2 (E V) (F at the last step)
+    float* Vc = Va;
+    float* Vn = Vb;
+    for (int s = 0; s < a.steps; ++s) {
+      float acc[4][8];
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 8; ++c) acc[r][c] = 0.f;
+#pragma unroll 4
+      for (int j = 0; j < NP; ++j) {
+        const float4 e = *reinterpret_cast<const float4*>(Et + j * NP + 4 * ig);
+        const float* vr = Vc + j * TV + ((vg ^ (j >> 2)) & 15) * 8;
+        const float4 v0 = *reinterpret_cast<const float4*>(vr);
+        const float4 v1 = *reinterpret_cast<const float4*>(vr + 4);
+        const float ev[4] = {e.x, e.y, e.z, e.w};
+        const float vv[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+          for (int c = 0; c < 8; ++c) acc[r][c] = fmaf(ev[r], vv[c], acc[r][c]);
       }
       const bool last = s == a.steps - 1;
 #pragma unroll
-      for (int i = 0; i < NP; ++i) col[i][t] = acc[i] * (last ? F[i] : F[i] * F[i]);
-    }
-    float sum = 0.f;
+      for (int r = 0; r < 4; ++r) {
+        const int i = 4 * ig + r;
+        const int off = i * TV + ((vg ^ ig) & 15) * 8;
+        const float4 f0 = *reinterpret_cast<const float4*>(F + off);
+        const float4 f1 = *reinterpret_cast<const float4*>(F + off + 4);
+        float w[8] = {f0.x, f0.y, f0.z, f0.w, f1.x, f1.y, f1.z, f1.w};
 #pragma unroll
-    for (int i = 0; i < NP; ++i) {
-      if (i < a.n_o) {
-        const float tau = fmaf(wx, nv[i][0], fmaf(wy, nv[i][1], wz * nv[i][2]));
-        const float hv = r2 > 0.f ? eval_h<EV>(a.h, tau * ri) : a.h.c0;
-        sum = fmaf(hv, col[i][t], sum);
+        for (int c = 0; c < 8; ++c) w[c] = acc[r][c] * (last ? w[c] : w[c] * w[c]);
+        *reinterpret_cast<float4*>(Vn + off) = make_float4(w[0], w[1], w[2], w[3]);
+        *reinterpret_cast<float4*>(Vn + off + 4) = make_float4(w[4], w[5], w[6], w[7]);
+      }
+      __syncthreads();
+      float* tmp = Vc;
+      Vc = Vn;
+      Vn = tmp;
+    }
+    // ---- m = n^3 h^T V per slot (products, then column sums)
+    for (int p = t; p < NP * TV; p += NT) {
+      const int i = p / TV, q = p % TV;
+      float hv = 0.f;
+      if (vox[q] >= 0 && i < a.n_o) {
+        const float tau = fmaf(geo[q], nv[3 * i], fmaf(geo[TV + q], nv[3 * i + 1], geo[2 * TV + q] * nv[3 * i + 2]));
+        hv = geo[4 * TV + q] > 0.f ? eval_h<EV>(a.h, tau * geo[3 * TV + q]) : a.h.c0;
+      }
+      Vn[i * TV + swz(i, q)] = hv * Vc[i * TV + swz(i, q)];
+    }
+    __syncthreads();
+    for (int q = t; q < TV; q += NT) {
+      if (vox[q] < 0) continue;
+      float sum = 0.f;
+      for (int i = 0; i < a.n_o; ++i) sum += Vn[i * TV + swz(i, q)];
+      const float m = sum * a.n3;
+      const float2 fh = a.fh[vox[q]];
+      a.A[vox[q]] = make_float2(fh.x * m, fh.y * m);
+      if (mvox[q] >= 0) {
+        const float2 fm = a.fh[mvox[q]];
+        a.A[mvox[q]] = make_float2(fm.x * m, fm.y * m);
       }
     }
-    const float2 fh = a.fh[v];
-    const float m = sum * a.n3;
-    a.A[v] = make_float2(fh.x * m, fh.y * m);
   }
 }
 
@@ -113,16 +187,53 @@ cudaError_t launch_np(const EnhanceArgs& a, int ev, cudaStream_t s) {
   int dev = 0, nsm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  const long long nvox = (long long)a.nz * a.ny * a.nx;
-  const long long need = (nvox + kEThreads - 1) / kEThreads;
-  const int grid = (int)std::max(1LL, std::min(need, (long long)nsm * 8));
   constexpr size_t sm = enhance_smem<NP>();
   auto k = ev == 0 ? enhance_kernel<NP, 0> : (ev == 1 ? enhance_kernel<NP, 1> : enhance_kernel<NP, 2>);
-  const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
-  k<<<grid, kEThreads, sm, s>>>(a);
+  int per_sm = 1;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 4 * NP, sm);
+  if (e != cudaSuccess) return e;
+  const int ntiles = (a.n_in + kTV - 1) / kTV;
+  const int grid = std::max(1, std::min(ntiles, nsm * std::max(per_sm, 1)));
+  k<<<grid, 4 * NP, sm, s>>>(a);
   return cudaGetLastError();
 }
+
+}  // namespace
+
+std::vector<int4> ball_segments(int nz, int ny, int nx, bool half, int* n_in) {
+  const double pi = kPiH, lim = pi * pi * (1.0 + 1e-12);
+  std::vector<int4> seg;
+  int total = 0;
+  auto sgn = [](int k, int n) { return k >= (n + 1) / 2 ? k - n : k; };
+  for (int z = 0; z < nz; ++z) {
+    const int kz = sgn(z, nz);
+    for (int y = 0; y < ny; ++y) {
+      const int ky = sgn(y, ny);
+      if (half && (kz < 0 || (kz == 0 && ky < 0))) continue;
+      const double wz = 2.0 * pi * kz / nz, wy = 2.0 * pi * ky / ny;
+      const double c = wz * wz + wy * wy;
+      if (!(c < lim)) continue;
+      int amax = (nx - 1) / 2;   // largest positive signed index
+      int ar = 0;
+      while (ar + 1 <= amax) {
+        const double wx = 2.0 * pi * (ar + 1) / nx;
+        if (!(wx * wx + c < lim)) break;
+        ++ar;
+      }
+      const bool origin_row = half && kz == 0 && ky == 0;
+      const int kx0 = origin_row ? 0 : -ar;
+      const int cnt = ar - kx0 + 1;
+      seg.push_back(make_int4(z, y, kx0, total));
+      total += cnt;
+    }
+  }
+  *n_in = total;
+  return seg;
+}
+
+namespace {
 
 // ---- host: discrete Laplace-Beltrami propagator (FP64) --------------------
 // Orthonormal real spherical harmonics up to degree l at the unit vectors:

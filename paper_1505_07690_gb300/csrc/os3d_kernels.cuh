@@ -103,7 +103,11 @@ cudaError_t launch_soft_slots(const PassArgs& a, long long nvox, cudaStream_t s)
 constexpr int kMaxOrientE = 68;
 struct EnhanceArgs {
   const float2* fh;           // f_hat G / n^3
-  float2* A;                  // out: fh * n^3 h^T E h (then x G/(n^3 max(M,eps)), IDFT)
+  float2* A;                  // out: fh * n^3 h^T E h (then x G/(n^3 max(M,eps)), IDFT);
+                              // zero on entry outside the listed frequencies
+  const int4* seg;            // in-ball row segments {z, y, kx0, first index}
+  int nseg, n_in;             // segments; listed frequencies
+  int mirror;                 // 1: the list covers half the ball, results go to w and -w
   int nz, ny, nx;
   float wz, wy, wx;           // 2 pi / n per axis
   float n3;                   // nz ny nx
@@ -116,6 +120,11 @@ struct EnhanceArgs {
   HEval h;
 };
 cudaError_t launch_enhance(const EnhanceArgs& a, int ev, cudaStream_t s);
+// host: the frequencies inside the ball |w| < pi (a superset by 1e-12 in
+// |w|^2) as row segments {z, y, kx0, first index}: rows of constant (kz, ky)
+// with kx in [kx0, -kx0] (or [0, a] for the row through the origin when
+// `half`); with `half` only kz > 0, or kz = 0 and ky > 0, and that half row.
+std::vector<int4> ball_segments(int nz, int ny, int nx, bool half, int* n_in);
 // host: exp(tau L) of the discrete Laplace-Beltrami operator (n x n, FP64);
 // returns the spherical-harmonic degree used, or -1
 int angular_propagator(const double* V, int n, int sh_degree, double tau, std::vector<double>& E);
