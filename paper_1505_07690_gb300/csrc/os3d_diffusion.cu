@@ -29,19 +29,21 @@ constexpr double kPiH = 3.141592653589793238462643383279502884;
 // One CTA per tile of TV = 128 listed frequencies, 4 NP threads; NP = the
 // orientation count padded to a multiple of 4. Per Strang step each thread
 // accumulates a 4 (orientations) x 8 (frequencies) tile of E V from shared
-// memory, so every propagator value it loads feeds 8 FMAs. Vectors are stored
-// [orientation][frequency] with the 8-frequency groups XOR-swizzled by the
-// orientation quad to spread the tile writes over the banks.
+// memory, so every propagator value it loads feeds 8 FMAs; the tile is written
+// back in place after a barrier. Vectors are stored [orientation][frequency]
+// with the float4 columns XOR-swizzled by the orientation quad, so that the
+// tile writes of the lanes (consecutive quads) fall on distinct banks.
 constexpr int kTV = 128;
 
 template <int NP>
 constexpr size_t enhance_smem() {
-  return sizeof(float) * ((size_t)NP * NP + 3 * (size_t)NP * kTV + 3 * NP + 5 * kTV) +
+  return sizeof(float) * ((size_t)NP * NP + 2 * (size_t)NP * kTV + 3 * NP + 5 * kTV) +
          sizeof(int) * 2 * kTV;
 }
 
-__device__ __forceinline__ int swz(int i, int q) {
-  return ((((q >> 3) ^ (i >> 2)) & 15) << 3) | (q & 7);
+// offset of element (i, q) of a [NP][kTV] vector array
+__device__ __forceinline__ int vofs(int i, int q) {
+  return i * kTV + ((((q >> 2) ^ (i >> 2)) & 7) | ((q >> 2) & ~7)) * 4 + (q & 3);
 }
 
 template <int NP, int EV>
@@ -50,9 +52,8 @@ enhance_kernel(const __grid_constant__ EnhanceArgs a) {
   constexpr int NT = 4 * NP, TV = kTV, NQ = NP / 4;
   extern __shared__ __align__(16) float esm[];
   float* Et = esm;                       // Et[j * NP + i] = E[i][j]
-  float* Va = Et + NP * NP;              // [i][q], two buffers
-  float* Vb = Va + NP * TV;
-  float* F = Vb + NP * TV;               // half-step factors exp(-dt/2 r_i)
+  float* V = Et + NP * NP;               // [i][q] (swizzled, see vofs)
+  float* F = V + NP * TV;                // half-step factors exp(-dt/2 r_i)
   float* nv = F + NP * TV;               // orientations (3 per row)
   float* geo = nv + 3 * NP;              // wx, wy, wz, 1/|w|, |w|^2 per slot
   int* vox = reinterpret_cast<int*>(geo + 5 * TV);
@@ -112,51 +113,54 @@ enhance_kernel(const __grid_constant__ EnhanceArgs a) {
         f = expf(-a.half_dt * fmaf(a.D11, r2 - tau * tau, a.D33 * tau * tau));
         if (i < a.n_o) hv = r2 > 0.f ? eval_h<EV>(a.h, tau * geo[3 * TV + q]) : a.h.c0;
       }
-      F[i * TV + swz(i, q)] = f;
-      Va[i * TV + swz(i, q)] = hv * f;
+      F[vofs(i, q)] = f;
+      V[vofs(i, q)] = hv * f;
     }
     __syncthreads();
     // ---- K Strang steps: V <- F^2 (E V) (F at the last step)
-    float* Vc = Va;
-    float* Vn = Vb;
     for (int s = 0; s < a.steps; ++s) {
       float acc[4][8];
 #pragma unroll
       for (int r = 0; r < 4; ++r)
 #pragma unroll
         for (int c = 0; c < 8; ++c) acc[r][c] = 0.f;
-#pragma unroll 4
-      for (int j = 0; j < NP; ++j) {
-        const float4 e = *reinterpret_cast<const float4*>(Et + j * NP + 4 * ig);
-        const float* vr = Vc + j * TV + ((vg ^ (j >> 2)) & 15) * 8;
-        const float4 v0 = *reinterpret_cast<const float4*>(vr);
-        const float4 v1 = *reinterpret_cast<const float4*>(vr + 4);
-        const float ev[4] = {e.x, e.y, e.z, e.w};
-        const float vv[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+      // rows j = 4 jq .. 4 jq + 3 share the swizzle of their quad jq
+#pragma unroll 1
+      for (int jq = 0; jq < NP / 4; ++jq) {
+        const int o0 = vofs(4 * jq, 8 * vg), o1 = vofs(4 * jq, 8 * vg + 4);
+        const float* er = Et + 4 * jq * NP + 4 * ig;
 #pragma unroll
-        for (int r = 0; r < 4; ++r)
+        for (int jj = 0; jj < 4; ++jj) {
+          const float4 e = *reinterpret_cast<const float4*>(er + jj * NP);
+          const float4 v0 = *reinterpret_cast<const float4*>(V + o0 + jj * kTV);
+          const float4 v1 = *reinterpret_cast<const float4*>(V + o1 + jj * kTV);
+          const float ev[4] = {e.x, e.y, e.z, e.w};
+          const float vv[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
 #pragma unroll
-          for (int c = 0; c < 8; ++c) acc[r][c] = fmaf(ev[r], vv[c], acc[r][c]);
+          for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int c = 0; c < 8; ++c) acc[r][c] = fmaf(ev[r], vv[c], acc[r][c]);
+        }
       }
       const bool last = s == a.steps - 1;
+      __syncthreads();   // every thread has read V
 #pragma unroll
       for (int r = 0; r < 4; ++r) {
         const int i = 4 * ig + r;
-        const int off = i * TV + ((vg ^ ig) & 15) * 8;
-        const float4 f0 = *reinterpret_cast<const float4*>(F + off);
-        const float4 f1 = *reinterpret_cast<const float4*>(F + off + 4);
-        float w[8] = {f0.x, f0.y, f0.z, f0.w, f1.x, f1.y, f1.z, f1.w};
 #pragma unroll
-        for (int c = 0; c < 8; ++c) w[c] = acc[r][c] * (last ? w[c] : w[c] * w[c]);
-        *reinterpret_cast<float4*>(Vn + off) = make_float4(w[0], w[1], w[2], w[3]);
-        *reinterpret_cast<float4*>(Vn + off + 4) = make_float4(w[4], w[5], w[6], w[7]);
+        for (int hh = 0; hh < 2; ++hh) {
+          const int off = vofs(i, 8 * vg + 4 * hh);
+          const float4 f = *reinterpret_cast<const float4*>(F + off);
+          const float w0 = last ? f.x : f.x * f.x, w1 = last ? f.y : f.y * f.y;
+          const float w2 = last ? f.z : f.z * f.z, w3 = last ? f.w : f.w * f.w;
+          *reinterpret_cast<float4*>(V + off) =
+              make_float4(acc[r][4 * hh] * w0, acc[r][4 * hh + 1] * w1, acc[r][4 * hh + 2] * w2,
+                          acc[r][4 * hh + 3] * w3);
+        }
       }
       __syncthreads();
-      float* tmp = Vc;
-      Vc = Vn;
-      Vn = tmp;
     }
-    // ---- m = n^3 h^T V per slot (products, then column sums)
+    // ---- m = n^3 h^T V per slot (products in place, then column sums)
     for (int p = t; p < NP * TV; p += NT) {
       const int i = p / TV, q = p % TV;
       float hv = 0.f;
@@ -164,13 +168,13 @@ enhance_kernel(const __grid_constant__ EnhanceArgs a) {
         const float tau = fmaf(geo[q], nv[3 * i], fmaf(geo[TV + q], nv[3 * i + 1], geo[2 * TV + q] * nv[3 * i + 2]));
         hv = geo[4 * TV + q] > 0.f ? eval_h<EV>(a.h, tau * geo[3 * TV + q]) : a.h.c0;
       }
-      Vn[i * TV + swz(i, q)] = hv * Vc[i * TV + swz(i, q)];
+      V[vofs(i, q)] *= hv;
     }
     __syncthreads();
     for (int q = t; q < TV; q += NT) {
       if (vox[q] < 0) continue;
       float sum = 0.f;
-      for (int i = 0; i < a.n_o; ++i) sum += Vn[i * TV + swz(i, q)];
+      for (int i = 0; i < a.n_o; ++i) sum += V[vofs(i, q)];
       const float m = sum * a.n3;
       const float2 fh = a.fh[vox[q]];
       a.A[vox[q]] = make_float2(fh.x * m, fh.y * m);
