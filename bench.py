@@ -29,6 +29,9 @@ import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
+# the oracle legs are reported as single-core: keep numpy's BLAS to one thread
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
 
 WORKLOAD = "splines128_no162"
 METRIC = "OS transform voxel·orientations/s (fwd+inv, FP32) at 128³×162; p50/p99 latency"
@@ -50,6 +53,9 @@ def _args():
                          "of the mixed-size workload and report p50/p99 latency")
     ap.add_argument("--load", type=float, default=0.8,
                     help="--serve arrival rate as a fraction of the measured capacity")
+    ap.add_argument("--precision", action="store_true",
+                    help="instead of the headline: reconstruction error of complex64 and BF16 "
+                         "scores at 256^3 x 42 against the exact result")
     ap.add_argument("--workload", default=WORKLOAD,
                     help="named synthetic workload (default: the 128^3 x 162 headline)")
     return ap.parse_args()
@@ -215,6 +221,17 @@ def _peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
+def _max_over_ranks(value, device):
+    """The maximum of ``value`` over the ranks of the default process group
+    (the value itself when there is none)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], device=device, dtype=torch.float64)
+    if dist.is_available() and dist.is_initialized():
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 # ---------------------------------------------------------------------------
 def run_ours(args):
     import numpy as np
@@ -273,11 +290,7 @@ def run_ours(args):
     barrier()
     clk = clocks.stop()
     step_ms = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
-    total_ms = ev[0].elapsed_time(ev[-1])
-    t = torch.tensor([total_ms], device="cuda")
-    if world > 1:
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-    total_ms = float(t.item())
+    total_ms = _max_over_ranks(ev[0].elapsed_time(ev[-1]), "cuda")
     value = world * nvox * n_o * args.steps / (total_ms / 1e3)
 
     # ---- end to end: host buffers through the public API, copies timed
@@ -299,11 +312,8 @@ def run_ours(args):
         e2e_step()
     e1.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1)
-    t = torch.tensor([e2e_ms], device="cuda")
-    if world > 1:
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-    e2e_value = world * nvox * n_o * args.steps / (float(t.item()) / 1e3)
+    e2e_ms = _max_over_ranks(e0.elapsed_time(e1), "cuda")
+    e2e_value = world * nvox * n_o * args.steps / (e2e_ms / 1e3)
 
     # ---- per-kernel durations (CUDA events around every launch, same stream)
     os3d.os3d_profile_reset()
@@ -511,6 +521,65 @@ def run_serve(args):
     return 0
 
 
+# ---------------------------------------------------------------------------
+# precision form: complex64 and BF16 storage of U against the exact result
+# ---------------------------------------------------------------------------
+def run_precision(args):
+    """256^3, 40 spline tubes, 42 orientations, L = 20. For each storage
+    format: the relative L2 error of W^-1 W f against the exactly known
+    IDFT[1_ball f_hat] (numpy FP64), and of the BF16 score against the
+    complex64 one; plus the forward+inverse time of each format."""
+    import numpy as np
+    import torch
+    from paper_1505_07690_gb300 import build, os3d, synth
+    build.build()
+    name = "splines256_no42"
+    w = synth.WORKLOADS[name]
+    dims = w["shape"]
+    f_np = synth.workload_volume(name)
+    fh = np.fft.fftn(f_np.astype(np.float64))
+    k = [np.fft.fftfreq(n) * 2 * np.pi for n in dims]
+    r2 = k[0][:, None, None] ** 2 + k[1][None, :, None] ** 2 + k[2][None, None, :] ** 2
+    fb = np.fft.ifftn(fh * (r2 < np.pi ** 2)).real
+    V = os3d.os3d_icosa_orientations(w["subdiv"])
+    bank = os3d.os3d_make_wavelets(dims, V, os3d.os3d_default_params(L=w["L"]))
+    f = torch.from_numpy(f_np).cuda()
+    out = {}
+    Uc = None
+    for fmt in ("c64", "bf16"):
+        U = os3d.new_score(bank, 1, bf16=(fmt == "bf16"))
+        fr = torch.empty_like(f)
+        for _ in range(max(args.warmup, 3)):
+            os3d.os3d_forward(bank, f, U)
+            os3d.os3d_inverse(bank, U, fr)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(args.steps):
+            os3d.os3d_forward(bank, f, U)
+            os3d.os3d_inverse(bank, U, fr)
+        b.record()
+        torch.cuda.synchronize()
+        err = float(np.linalg.norm(fr.cpu().numpy() - fb) / np.linalg.norm(fb))
+        rec = {"recon_rel_l2_vs_exact": err, "ms_per_fwd_inv": a.elapsed_time(b) / args.steps,
+               "score_gb": U.numel() * U.element_size() / 1e9}
+        if fmt == "c64":
+            Uc = U[0, :4].clone()
+        else:
+            Ub = torch.view_as_complex(U[0, :4].float().contiguous())
+            rec["score_rel_l2_vs_c64"] = float(torch.linalg.vector_norm(Ub - Uc) /
+                                               torch.linalg.vector_norm(Uc))
+        out[fmt] = rec
+        del U
+        torch.cuda.empty_cache()
+    line = {"metric": "precision form: relative L2 error of the reconstruction per score format",
+            "data": "synthetic", "dtype": "f32",
+            "config": {"workload": name, "dims": list(dims), "n_o": len(V), "L": w["L"]},
+            "formats": out, "steps": args.steps, "warmup": args.warmup}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     global WORKLOAD
     args = _args()
@@ -519,6 +588,8 @@ def main():
         return run_reference(args)
     if args.serve:
         return run_serve(args)
+    if args.precision:
+        return run_precision(args)
     return run_ours(args)
 
 
