@@ -86,6 +86,15 @@ __device__ __forceinline__ void cluster_sync_acqrel() {
   asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" :::
                    "memory");
 }
+// Asynchronous prefetch of `bytes` (multiple of 16, 16-byte aligned) of
+// global memory into L2; no completion to wait for.
+__device__ __forceinline__ void prefetch_l2(const void* p, unsigned bytes) {
+  asm volatile(
+      "{\n\t.reg .u64 ga;\n\t"
+      "cvta.to.global.u64 ga, %0;\n\t"
+      "cp.async.bulk.prefetch.L2.global [ga], %1;\n\t}" ::"l"(p), "r"(bytes)
+      : "memory");
+}
 __device__ __forceinline__ unsigned cluster_rank() {
   unsigned r;
   asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
@@ -402,6 +411,20 @@ xy_kernel(const __grid_constant__ PassArgs a) {
       }
     }
     __syncthreads();
+    // the input rows of this CTA's next unit go to L2 while this one runs
+    if (t == 0 && (MODE == XY_FWD_SCORE || MODE == XY_INV_SCORE) && u + ncl < nunits) {
+      const int zn = (u + ncl) % a.nz, sn = (u + ncl) / a.nz;
+      const long long rows = (long long)zn * P + (long long)h * NYH * NX;
+      constexpr unsigned esz = (MODE == XY_INV_SCORE && UBF16) ? 4u : 8u;
+      constexpr unsigned bytes = (unsigned)(NYH * NX) * esz;
+      const char* base = reinterpret_cast<const char*>(a.in);
+      if constexpr (MODE == XY_FWD_SCORE) {
+        prefetch_l2(base + 8 * ((long long)sn * a.slot_stride + rows), bytes);
+      } else {
+        prefetch_l2(base + esz * (a.ua[sn] + rows), bytes);
+        if (a.ub[sn] >= 0) prefetch_l2(base + esz * (a.ub[sn] + rows), bytes);
+      }
+    }
     // ---- x direction, step 2; outputs go to the owner of their column
     {
       float2 w[C::JX3][R2x];
@@ -532,6 +555,12 @@ xy_soft_kernel(const __grid_constant__ PassArgs a) {
   for (int u = cl; u < nunits; u += ncl) {
     const int z = u % a.nz, s = u / a.nz;
     float2* T = reinterpret_cast<float2*>(a.out) + (long long)s * a.slot_stride + (long long)z * P;
+    if (t == 0 && u + ncl < nunits) {
+      const int zn = (u + ncl) % a.nz, sn = (u + ncl) / a.nz;
+      prefetch_l2(reinterpret_cast<const float2*>(a.out) + (long long)sn * a.slot_stride +
+                      (long long)zn * P + (long long)h * NYH * NX,
+                  (unsigned)(NYH * NX * sizeof(float2)));
+    }
     const float scale = a.ub[s] >= 0 ? 2.f : 1.f;
     // ---- (1) IDFT along x, step 1 (global -> registers -> shared)
     {
