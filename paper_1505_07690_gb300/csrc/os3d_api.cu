@@ -739,6 +739,9 @@ PassArgs args_base(const os3d_bank* b) {
   a.slot_stride = b->nvox;
   a.nslots = 1;
   a.h = b->h;
+  // tiles outside the disc are skipped only where the cluster plane pass
+  // (which honours the skip) consumes or produces the block intermediates
+  a.disc = xy_supported(b->dims[1], b->dims[2]) ? 1 : 0;
   for (int j = 0; j < kMaxSlots; ++j) a.ub[j] = -1;
   return a;
 }

@@ -51,6 +51,9 @@ struct PassArgs {
   int nslots;
   int accumulate;             // Z_INV_SCORE: 0 -> A = sum, 1 -> A += sum
   float power;                // XY_SOFT / soft threshold: exponent p > 0
+  int disc;                   // 1: 16-column z tiles outside the disc |w_xy| < pi are
+                              // skipped by the z-passes and read as zero / not written
+                              // by the plane passes (cluster plane path only)
   float nvec[kMaxSlots][3];   // orientation n_a (x, y, z) of each slot
   HEval h;
 };

@@ -25,6 +25,18 @@ namespace os3d {
 
 __device__ __forceinline__ int signed_index(int k, int n) { return k >= (n + 1) / 2 ? k - n : k; }
 
+// True when every column (kx, ky) of the 16-wide z tile holding DFT index x
+// lies strictly outside the disc |w_xy| < pi, where psi_hat vanishes for
+// every kz: 4 (kx^2/nx^2 + ky^2/ny^2) > 1 for the tile's smallest |kx|
+// (exact integer test; the boundary itself counts as inside).
+__device__ __forceinline__ bool tile_outside(int x, int y, int nx, int ny) {
+  const int x0 = x & ~(kTileX - 1);
+  const int kx = x0 < (nx + 1) / 2 ? x0 : (x0 + kTileX - 1 < (nx + 1) / 2 ? 0 : nx - (x0 + kTileX - 1));
+  const long long ky = signed_index(y, ny);
+  const long long a = (long long)kx * kx * ny * ny + ky * ky * (long long)nx * nx;
+  return 4 * a > (long long)nx * nx * ny * ny;
+}
+
 // Angular profile h at t = w_hat . n. EV 0 / 1: h(t) = E(v) + t O(v), v = t^2 - 1/2,
 // E and O in the monomial basis of v by Horner's rule (9 + 8 or 13 + 12
 // coefficients), chosen on the host only when the coefficients show no
@@ -124,6 +136,16 @@ z_kernel(const __grid_constant__ PassArgs a) {
   const long long plane = (long long)a.ny * a.nx;
   const long long col = (long long)y * a.nx + x;
 
+  if constexpr (MODE == Z_FWD_SCORE || MODE == Z_INV_SCORE) {
+    if (a.disc && tile_outside(x, y, a.nx, a.ny)) {
+      // psi_hat = 0 on the whole tile: the forward leaves T unwritten (the
+      // plane pass reads zeros there); the inverse's sum stays zero
+      if (MODE == Z_INV_SCORE && !a.accumulate)
+        for (int z = n2; z < NZ; z += R2)
+          reinterpret_cast<float2*>(a.out)[(long long)z * plane + col] = make_float2(0.f, 0.f);
+      return;
+    }
+  }
   fill_twiddles<NZ, DIR>(tws);
   const float wy = float(signed_index(y, a.ny)) * a.wy;
   const float wx = float(signed_index(x, a.nx)) * a.wx;
@@ -400,6 +422,10 @@ xy_kernel(const __grid_constant__ PassArgs a) {
             float2 q = load_u<UBF16>(a.in, ia + e);
             if (ib >= 0) q = cadd(q, cconj(load_u<UBF16>(a.in, ib + e)));
             v[n1] = q;
+          } else if constexpr (MODE == XY_FWD_SCORE) {
+            v[n1] = (a.disc && tile_outside(n2 + R2x * n1, h * NYH + r, NX, NY))
+                        ? make_float2(0.f, 0.f)
+                        : reinterpret_cast<const float2*>(a.in)[ia + e];
           } else {
             v[n1] = reinterpret_cast<const float2*>(a.in)[ia + e];
           }
@@ -502,6 +528,9 @@ xy_kernel(const __grid_constant__ PassArgs a) {
             if (ob >= 0) store_u<UBF16>(a.out, ob + e, cconj(w[k2]));
           } else if constexpr (MODE == XY_INV_REAL) {
             reinterpret_cast<float*>(a.out)[o + e] = w[k2].x;
+          } else if constexpr (MODE == XY_INV_SCORE) {
+            if (!(a.disc && tile_outside(h * NXH + c, k1 + R1y * k2, NX, NY)))
+              reinterpret_cast<float2*>(a.out)[o + e] = w[k2];
           } else {
             reinterpret_cast<float2*>(a.out)[o + e] = w[k2];
           }
@@ -574,7 +603,10 @@ xy_soft_kernel(const __grid_constant__ PassArgs a) {
         const float2* row = T + (long long)(h * NYH + r) * NX;
         float2 v[R1x];
 #pragma unroll
-        for (int n1 = 0; n1 < R1x; ++n1) v[n1] = row[n2 + R2x * n1];
+        for (int n1 = 0; n1 < R1x; ++n1)
+          v[n1] = (a.disc && tile_outside(n2 + R2x * n1, h * NYH + r, NX, NY))
+                      ? make_float2(0.f, 0.f)
+                      : row[n2 + R2x * n1];
         dft<R1x, +1>(v);
 #pragma unroll
         for (int k1 = 0; k1 < R1x; ++k1)
@@ -720,7 +752,9 @@ xy_soft_kernel(const __grid_constant__ PassArgs a) {
       dft<R2x, -1>(w);
       float2* row = T + (long long)(h * NYH + r) * NX;
 #pragma unroll
-      for (int k2 = 0; k2 < R2x; ++k2) row[k1 + R1x * k2] = w[k2];
+      for (int k2 = 0; k2 < R2x; ++k2)
+        if (!(a.disc && tile_outside(k1 + R1x * k2, h * NYH + r, NX, NY)))
+          row[k1 + R1x * k2] = w[k2];
     }
     __syncthreads();    // work is rewritten by the next unit
   }
