@@ -504,6 +504,7 @@ def run_serve(args):
         out.append(srv.submit(pool[sh][k], sd))
     drain(out, lat, True)
     t_run = time.perf_counter() - t0
+    done, captured, replayed = srv.stats()
     srv.close()
     line = {
         "metric": "serving: forward+inverse per request, mixed sizes, Poisson arrivals; p50/p99 latency",
@@ -512,6 +513,7 @@ def run_serve(args):
                        "mean": float(np.mean(lat))},
         "requests": len(reqs), "requests_per_s": len(reqs) / t_run,
         "capacity_requests_per_s": capacity, "load": args.load,
+        "graphs": {"captured": captured, "replays": replayed, "completed": done},
         "dtype": "f32", "data": "synthetic",
         "config": {"workload": "serve_mix", "shapes": SERVE_SHAPES, "n_o": [42, 162], "L": 16,
                    "arrival": "poisson", "udtype": "bf16x2" if args.bf16 else "c64",

@@ -263,10 +263,17 @@ typedef struct {
   size_t arena_bytes;  /* device memory for in-flight requests                  */
   int max_inflight;    /* concurrent requests (streams), 1..64                  */
   int udtype;          /* score storage of every request: OS3D_U_C64 or BF16X2  */
+  int use_graphs;      /* 1: the kernels of forward + inverse for one (bank, arena
+                          offset) are captured as a CUDA graph when that pair occurs
+                          for the second time and replayed by every later request
+                          on it (up to 512 graphs, then the cache is cleared); a
+                          pair seen once runs with direct launches. 0: direct
+                          launches only                                            */
 } os3d_server_config;
 typedef struct os3d_server os3d_server;
 
-/* arena_bytes = 16 GiB, max_inflight = 4, udtype = OS3D_U_C64. Host only. */
+/* arena_bytes = 16 GiB, max_inflight = 4, udtype = OS3D_U_C64, use_graphs = 1.
+ * Host only. */
 os3d_status os3d_server_default_config(os3d_server_config* cfg);
 /* Errors: EINVAL (config out of range), ENOMEM (arena), ECUDA. p may be NULL
  * (defaults). */
@@ -283,6 +290,10 @@ os3d_status os3d_server_submit(os3d_server* s, const int dims[3], int subdiv, co
  * ticket is released. */
 os3d_status os3d_server_wait(os3d_server* s, long long ticket, double timeout_s,
                              double* latency_ms);
+/* Counters since creation: completed requests, graphs captured, graph replays
+ * (requests served by an already captured graph). Any pointer may be NULL. */
+os3d_status os3d_server_stats(os3d_server* s, long long* completed, long long* graphs_captured,
+                              long long* graph_replays);
 /* Finishes every queued and in-flight request, then frees the server. */
 os3d_status os3d_server_destroy(os3d_server* s);
 

@@ -386,6 +386,13 @@ cudaError_t counted_launch(int kind, cudaStream_t s, F&& launch) {
   return e;
 }
 
+}  // namespace
+
+bool os3d::profiling_enabled() { return g_profile.load() != 0; }
+void os3d::add_launch_count(unsigned long long n) { g_launches.fetch_add(n); }
+
+namespace {
+
 os3d_status current_device_matches(const os3d_bank* b) {
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess) return OS3D_ECUDA;

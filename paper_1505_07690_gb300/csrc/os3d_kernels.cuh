@@ -132,6 +132,10 @@ std::vector<int4> ball_segments(int nz, int ny, int nx, bool half, int* n_in);
 // returns the spherical-harmonic degree used, or -1
 int angular_propagator(const double* V, int n, int sh_degree, double tau, std::vector<double>& E);
 
+// launch accounting shared with the serving engine (os3d_api.cu)
+bool profiling_enabled();
+void add_launch_count(unsigned long long n);
+
 // FP64 bank kernels
 cudaError_t launch_fit(const double* d_z, const double* d_w, int npts, int mode, int k,
                        double s_theta, int L, int n_o, int profile, double* d_out,

@@ -8,6 +8,11 @@
 // reconstruction. Completion is signalled by a host function enqueued behind
 // the copy. Wavelet banks are cached per (grid, orientation set); the arena
 // is allocated once at creation, so serving itself allocates no device memory.
+// With use_graphs, the kernel sequence of forward + inverse for one (bank,
+// arena offset) is captured into a CUDA graph the second time that pair
+// occurs (a pair seen once runs with direct launches, so one-off placements
+// pay no capture) and replayed for every later request on the same pair: one
+// launch instead of about fifty.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -22,6 +27,7 @@
 
 #include <cuda_runtime.h>
 #include "../../include/os3d.h"
+#include "os3d_kernels.cuh"
 
 namespace {
 
@@ -85,6 +91,12 @@ struct BankEntry {
   size_t ws_bytes = 0, score_bytes = 0;
 };
 
+struct GraphEntry {
+  cudaGraphExec_t exec = nullptr;
+  unsigned long long kernels = 0;   // kernel launches the graph replays
+};
+constexpr size_t kMaxGraphs = 512;
+
 }  // namespace
 
 struct os3d_server {
@@ -97,6 +109,9 @@ struct os3d_server {
   std::vector<std::shared_ptr<Request>> slot_req;   // in-flight request per stream slot
   cudaStream_t bank_stream = nullptr;
   std::map<std::tuple<int, int, int, int>, BankEntry> banks;
+  std::map<std::pair<const os3d_bank*, size_t>, GraphEntry> graphs;   // worker thread only
+  std::map<std::pair<const os3d_bank*, size_t>, int> seen;            // worker thread only
+  long long n_done = 0, n_captured = 0, n_replayed = 0;                // under mu
   std::deque<std::shared_ptr<Request>> pending;
   std::map<long long, std::shared_ptr<Request>> all;
   std::mutex mu;
@@ -116,6 +131,7 @@ struct os3d_server {
     std::lock_guard<std::mutex> lk(d->s->mu);
     d->r->t_done = Clock::now();
     d->r->done = true;
+    d->s->n_done += 1;
     d->s->cv.notify_all();
     d->s->done_cv.notify_all();
   }
@@ -160,15 +176,65 @@ struct os3d_server {
     void* ws = reinterpret_cast<char*>(fout) + align_up(nvox * sizeof(float));
     if (cudaMemcpyAsync(fin, r.f, nvox * sizeof(float), cudaMemcpyHostToDevice, s) != cudaSuccess)
       return OS3D_ECUDA;
-    os3d_status st = os3d_forward(e.bank, fin, 1, U, (os3d_udtype)cfg.udtype, ws, s);
-    if (st != OS3D_OK) return st;
-    st = os3d_inverse(e.bank, U, (os3d_udtype)cfg.udtype, 1, fout, ws, s);
-    if (st != OS3D_OK) return st;
+    auto transforms = [&]() {
+      os3d_status st = os3d_forward(e.bank, fin, 1, U, (os3d_udtype)cfg.udtype, ws, s);
+      if (st == OS3D_OK) st = os3d_inverse(e.bank, U, (os3d_udtype)cfg.udtype, 1, fout, ws, s);
+      return st;
+    };
+    const auto key = std::make_pair((const os3d_bank*)e.bank, r.off);
+    bool use_graph = false;
+    if (cfg.use_graphs && !os3d::profiling_enabled()) {
+      if (graphs.count(key)) {
+        use_graph = true;
+      } else {
+        if (seen.size() >= 8 * kMaxGraphs) seen.clear();
+        use_graph = seen[key]++ > 0;
+      }
+    }
+    if (use_graph) {
+      auto it = graphs.find(key);
+      if (it == graphs.end()) {
+        if (graphs.size() >= kMaxGraphs) drop_graphs();
+        GraphEntry g;
+        const unsigned long long l0 = os3d_launch_count();
+        if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+          return OS3D_ECUDA;
+        const os3d_status st = transforms();
+        cudaGraph_t graph = nullptr;
+        const cudaError_t ce = cudaStreamEndCapture(s, &graph);
+        if (st != OS3D_OK || ce != cudaSuccess) {
+          if (graph) cudaGraphDestroy(graph);
+          cudaGetLastError();
+          return st != OS3D_OK ? st : OS3D_ECUDA;
+        }
+        const cudaError_t ie = cudaGraphInstantiate(&g.exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ie != cudaSuccess) return OS3D_ECUDA;
+        // the capture counted its kernels once; the first replay executes them
+        g.kernels = os3d_launch_count() - l0;
+        it = graphs.emplace(key, g).first;
+        std::lock_guard<std::mutex> lk(mu);
+        n_captured += 1;
+      } else {
+        os3d::add_launch_count(it->second.kernels);
+        std::lock_guard<std::mutex> lk(mu);
+        n_replayed += 1;
+      }
+      if (cudaGraphLaunch(it->second.exec, s) != cudaSuccess) return OS3D_ECUDA;
+    } else {
+      const os3d_status st = transforms();
+      if (st != OS3D_OK) return st;
+    }
     if (cudaMemcpyAsync(r.f_out, fout, nvox * sizeof(float), cudaMemcpyDeviceToHost, s) !=
         cudaSuccess)
       return OS3D_ECUDA;
     if (cudaLaunchHostFunc(s, on_done, new Done{this, &r}) != cudaSuccess) return OS3D_ECUDA;
     return OS3D_OK;
+  }
+
+  void drop_graphs() {
+    for (auto& kv : graphs) cudaGraphExecDestroy(kv.second.exec);
+    graphs.clear();
   }
 
   void run() {
@@ -255,6 +321,7 @@ os3d_status os3d_server_default_config(os3d_server_config* c) {
   c->arena_bytes = (size_t)16 << 30;
   c->max_inflight = 4;
   c->udtype = OS3D_U_C64;
+  c->use_graphs = 1;
   return OS3D_OK;
 }
 
@@ -263,7 +330,8 @@ os3d_status os3d_server_create(const os3d_server_config* cfg, const os3d_params*
   if (!cfg || !out) return OS3D_EINVAL;
   *out = nullptr;
   if (cfg->arena_bytes < kAlign || cfg->max_inflight < 1 || cfg->max_inflight > 64 ||
-      (cfg->udtype != OS3D_U_C64 && cfg->udtype != OS3D_U_BF16X2))
+      (cfg->udtype != OS3D_U_C64 && cfg->udtype != OS3D_U_BF16X2) ||
+      (cfg->use_graphs != 0 && cfg->use_graphs != 1))
     return OS3D_EINVAL;
   auto s = std::make_unique<os3d_server>();
   s->cfg = *cfg;
@@ -331,6 +399,16 @@ os3d_status os3d_server_wait(os3d_server* s, long long ticket, double timeout_s,
   return st;
 }
 
+os3d_status os3d_server_stats(os3d_server* s, long long* completed, long long* graphs_captured,
+                              long long* graph_replays) {
+  if (!s) return OS3D_EINVAL;
+  std::lock_guard<std::mutex> lk(s->mu);
+  if (completed) *completed = s->n_done;
+  if (graphs_captured) *graphs_captured = s->n_captured;
+  if (graph_replays) *graph_replays = s->n_replayed;
+  return OS3D_OK;
+}
+
 os3d_status os3d_server_destroy(os3d_server* s) {
   if (!s) return OS3D_EINVAL;
   {
@@ -341,6 +419,7 @@ os3d_status os3d_server_destroy(os3d_server* s) {
   if (s->worker.joinable()) s->worker.join();
   for (auto& st : s->streams)
     if (st) cudaStreamSynchronize(st), cudaStreamDestroy(st);
+  s->drop_graphs();
   if (s->bank_stream) cudaStreamDestroy(s->bank_stream);
   for (auto& kv : s->banks) os3d_destroy_bank(kv.second.bank);
   if (s->arena_base) cudaFree(s->arena_base);

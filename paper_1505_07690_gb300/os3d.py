@@ -35,7 +35,7 @@ class os3d_diffusion(ctypes.Structure):
 
 class os3d_server_config(ctypes.Structure):
     _fields_ = [("arena_bytes", ctypes.c_size_t), ("max_inflight", ctypes.c_int),
-                ("udtype", ctypes.c_int)]
+                ("udtype", ctypes.c_int), ("use_graphs", ctypes.c_int)]
 
 
 class OS3DError(RuntimeError):
@@ -92,6 +92,9 @@ def lib():
                                          ctypes.POINTER(ctypes.c_longlong)]
         L.os3d_server_wait.argtypes = [vp, ctypes.c_longlong, d, ctypes.POINTER(d)]
         L.os3d_server_destroy.argtypes = [vp]
+        L.os3d_server_stats.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong),
+                                        ctypes.POINTER(ctypes.c_longlong),
+                                        ctypes.POINTER(ctypes.c_longlong)]
         L.os3d_kernel_kind_name.restype = ctypes.c_char_p
         L.os3d_kernel_kind_name.argtypes = [i]
         for name in ("os3d_default_params", "os3d_icosa_orientations", "os3d_make_wavelets",
@@ -103,7 +106,7 @@ def lib():
                      "os3d_server_destroy", "os3d_octa_orientations",
                      "os3d_approx_reconstruct", "os3d_project", "os3d_soft_threshold",
                      "os3d_upsilon", "os3d_default_diffusion", "os3d_enhance_linear",
-                     "os3d_angular_propagator"):
+                     "os3d_angular_propagator", "os3d_server_stats"):
             getattr(L, name).restype = i
         _lib = L
     return _lib
@@ -480,6 +483,13 @@ class Server:
         f_host, f_out = self._keep.pop(ticket)
         _check(st, "os3d_server_wait")
         return f_out, lat.value
+
+    def stats(self):
+        """(completed requests, graphs captured, graph replays)."""
+        v = [ctypes.c_longlong(0) for _ in range(3)]
+        _check(lib().os3d_server_stats(self.handle, *[ctypes.byref(x) for x in v]),
+               "os3d_server_stats")
+        return tuple(x.value for x in v)
 
     def close(self):
         if self.handle:

@@ -154,7 +154,10 @@ def test_injected_allocation_failure(L, monkeypatch):
 def test_server_config_checked_before_any_cuda_call(L):
     from paper_1505_07690_gb300 import os3d
     h = ctypes.c_void_p(0)
-    for field, val in (("max_inflight", 0), ("max_inflight", 65), ("udtype", 3), ("arena_bytes", 0)):
+    assert os3d.os3d_server_default_config().use_graphs == 1
+    assert L.os3d_server_stats(None, None, None, None) == 1
+    for field, val in (("max_inflight", 0), ("max_inflight", 65), ("udtype", 3), ("arena_bytes", 0),
+                       ("use_graphs", 2)):
         c = os3d.os3d_server_default_config(**{field: val})
         assert L.os3d_server_create(ctypes.byref(c), None, ctypes.byref(h)) == 1, field
     assert L.os3d_server_destroy(None) == 1

@@ -1,7 +1,7 @@
 """The serving engine (os3d_server_*): results equal direct calls, equal
-whether a request runs alone or amid others, admission by arena footprint,
-bounded waits. Failures are made on the host (a request that cannot fit, a
-wait that runs out), never on the GPU."""
+whether a request runs alone or amid others, with graph replay or direct
+launches, admission by arena footprint, bounded waits. Failures are made on
+the host (a request that cannot fit, a wait that runs out), never on the GPU."""
 import numpy as np
 import pytest
 
@@ -92,3 +92,34 @@ def test_admission_by_footprint_and_bounded_wait(M):
         assert e.value.status == 2
     finally:
         srv.close()
+
+
+def test_graph_replay_matches_direct_launches(M):
+    """Repeated requests replay the captured graph of their (bank, arena
+    offset); results equal those of a server launching directly."""
+    vols = _volumes()
+    outs = {}
+    for graphs in (1, 0):
+        srv = M.Server(M.os3d_server_default_config(arena_bytes=2 << 30, max_inflight=1,
+                                                    use_graphs=graphs),
+                       M.os3d_default_params(L=12))
+        try:
+            res = []
+            for _ in range(3):                       # the same sequence three times
+                for (d, sub), v in zip(MIX, vols):
+                    res.append(srv.wait(srv.submit(v, sub), 60.0)[0].numpy().copy())
+            stats = srv.stats()
+        finally:
+            srv.close()
+        outs[graphs] = res
+        assert stats[0] == 3 * len(MIX)
+        if graphs:
+            # one stream slot and one request at a time: every request lands at
+            # offset 0; each bank runs directly the first time, is captured the
+            # second time and replayed the third
+            assert stats[1] == len(set(MIX))
+            assert stats[2] == len(MIX)
+        else:
+            assert stats[1] == 0 and stats[2] == 0
+    for a, b in zip(outs[1], outs[0]):
+        assert np.array_equal(a, b)
