@@ -232,3 +232,53 @@ def test_precision_workload_sampled_c64_and_bf16(M):
     torch.cuda.empty_cache()
     Ub = M.os3d_forward(bank, fd, bf16=True)
     assert rel(_to_np(M.os3d_inverse(bank, Ub))[0], fb) <= TOL_BF16
+
+
+def test_degenerate_orientation_sets(M):
+    """One orientation (unpaired), and a single antipodal pair."""
+    dims = (32, 32, 32)
+    f = synth.straight_tubes(dims, 2, seed=51)
+    V = O.icosa_orientations(1)
+    _check_forward_inverse(M, dims, f, orient=V[:1].copy(), L=12)
+    _check_forward_inverse(M, dims, f, orient=np.stack([V[0], V[21]]), L=12)
+
+
+def test_isotropic_wavelet_closed_form(M):
+    """L = 0: h is the constant c_0, so every psi_hat_i = c_0 G and
+    U_i = IDFT[c_0 G f_hat] for all i, with c_0 = 1/sqrt(N_o) (the
+    normalisation); the inverse returns IDFT[1_ball f_hat]. Checked against
+    these closed forms, not the oracle."""
+    dims = (32, 32, 32)
+    f = synth.straight_tubes(dims, 3, seed=52)
+    V = O.icosa_orientations(1)
+    bank = M.os3d_make_wavelets(dims, V, _params(M, L=0))
+    b, c = M.os3d_bank_coefficients(bank)
+    assert abs(c[0] - 1.0 / np.sqrt(42.0)) < 1e-12
+    U = _to_np(M.os3d_forward(bank, _cuda(f)))[0]
+    fh = np.fft.fftn(f.astype(np.float64))
+    G = O.radial_ball(dims, 8, 0.8)
+    u0 = np.fft.ifftn(fh * G * c[0])
+    for i in (0, 7, 41):
+        assert rel(U[i], u0) <= TOL
+    wz, wy, wx = O.freq_grid(dims)
+    ball = np.sqrt(wz ** 2 + wy ** 2 + wx ** 2) < np.pi
+    fr = _to_np(M.os3d_inverse(bank, _cuda(U[None])))[0]
+    assert rel(fr, np.fft.ifftn(fh * ball).real) <= TOL
+
+
+@pytest.mark.parametrize("kw", [dict(N=0, L=12), dict(L=32, fit_mode=0), dict(L=28, k=3, s_theta=0.5)])
+def test_parameter_extremes(M, kw):
+    """N = 0 (plain Gaussian window), L = 32 and L = 28 (Chebyshev evaluation
+    of h), cubic B-spline profile."""
+    dims = (32, 32, 32)
+    f = synth.straight_tubes(dims, 3, seed=53)
+    _check_forward_inverse(M, dims, f, **kw)
+
+
+def test_batch_zero_is_rejected(M):
+    dims = (16, 16, 16)
+    bank, _ = _pair(M, dims, L=8)
+    import ctypes
+    L = M.lib()
+    assert L.os3d_forward(bank.handle, ctypes.c_void_p(1), 0, ctypes.c_void_p(1), 0, None, None) == 1
+    assert L.os3d_inverse(bank.handle, ctypes.c_void_p(1), 0, 0, ctypes.c_void_p(1), None, None) == 1
