@@ -895,7 +895,6 @@ os3d_status backward_impl(const os3d_bank* b, const void* U, int udtype, int bat
   const int nz = b->dims[0], ny = b->dims[1], nx = b->dims[2];
   const int nslots = (int)b->slot_a.size();
   const int tiles = ny * (nx / kTileX);
-  const long long n = b->nvox;
   for (int v = 0; v < batch; ++v) {
     if (b->p.overlap) OS3D_CK(fork_side(b, s));
     int q = 0;
@@ -929,7 +928,6 @@ os3d_status forward_impl(const os3d_bank* b, const float* f, int batch, void* U,
   const int nz = b->dims[0], ny = b->dims[1], nx = b->dims[2];
   const int nslots = (int)b->slot_a.size();
   const int tiles = ny * (nx / kTileX);
-  const long long n = b->nvox;
   for (int v = 0; v < batch; ++v) {
     // (a4) f_hat G / n^3
     const os3d_status st = prep_fhat(b, f, v, w, s);

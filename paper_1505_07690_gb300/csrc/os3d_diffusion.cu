@@ -23,7 +23,6 @@ namespace os3d {
 
 namespace {
 
-constexpr int kEThreads = 128;
 constexpr double kPiH = 3.141592653589793238462643383279502884;
 
 // One CTA per tile of TV = 128 listed frequencies, 4 NP threads; NP = the

@@ -123,3 +123,26 @@ def test_graph_replay_matches_direct_launches(M):
             assert stats[1] == 0 and stats[2] == 0
     for a, b in zip(outs[1], outs[0]):
         assert np.array_equal(a, b)
+
+
+def test_graph_replay_with_bf16_scores_and_streams(M):
+    """BF16 score storage, three stream slots, requests in a mix: a replaying
+    server returns what a directly launching one returns."""
+    vols = _volumes()
+    outs = {}
+    for graphs in (1, 0):
+        srv = M.Server(M.os3d_server_default_config(arena_bytes=2 << 30, max_inflight=3,
+                                                    udtype=M.OS3D_U_BF16X2, use_graphs=graphs),
+                       M.os3d_default_params(L=12))
+        try:
+            res = []
+            for _ in range(3):
+                tickets = [srv.submit(v, sub) for (d, sub), v in zip(MIX, vols)]
+                res += [srv.wait(t, 60.0)[0].numpy().copy() for t in tickets]
+            stats = srv.stats()
+        finally:
+            srv.close()
+        outs[graphs] = res
+        assert stats[0] == 3 * len(MIX)
+    for a, b in zip(outs[1], outs[0]):
+        assert np.array_equal(a, b)
