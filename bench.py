@@ -232,6 +232,78 @@ def _max_over_ranks(value, device):
     return float(t.item())
 
 
+def _cufft_compare(os3d, bank, V, dims, w, f, frec, steps, timed):
+    """Forward + exact inverse with torch.fft (cuFFT, batched over the N_o
+    orientations) and elementwise products with stored wavelets; the timing
+    and the relative L2 difference of its reconstruction from ours."""
+    import math
+    import torch
+    dev = f.device
+    _, c = os3d.os3d_bank_coefficients(bank)
+    minv = os3d.os3d_bank_minv(bank)
+    k = [torch.fft.fftfreq(n, device=dev, dtype=torch.float64) * 2 * math.pi for n in dims]
+    wz, wy, wx = k[0][:, None, None], k[1][None, :, None], k[2][None, None, :]
+    r2 = wz ** 2 + wy ** 2 + wx ** 2
+    N, gamma = bank.params.N, bank.params.gamma
+    x = r2 / (2 * (gamma * math.pi) ** 2 / (1 + 2 * N))
+    g = torch.zeros_like(x)
+    term = torch.ones_like(x)
+    for q in range(N + 1):
+        if q:
+            term = term * x / q
+        g = g + term
+    G = torch.where(r2 < math.pi ** 2, torch.exp(-x) * g, torch.zeros_like(x))
+    ri = torch.where(r2 > 0, torch.rsqrt(torch.where(r2 > 0, r2, torch.ones_like(r2))),
+                     torch.zeros_like(r2))
+    psi = torch.empty((len(V),) + tuple(dims), device=dev, dtype=torch.float32)
+    for i, (nx, ny, nz) in enumerate(V):
+        t = ((wx * nx + wy * ny + wz * nz) * ri).clamp(-1, 1)
+        pm, pl = torch.ones_like(t), t
+        h = c[0] * pm + (c[1] * pl if len(c) > 1 else 0)
+        for l in range(1, len(c) - 1):
+            pm, pl = pl, ((2 * l + 1) * t * pl - l * pm) / (l + 1)
+            h = h + c[l + 1] * pl
+        h = torch.where(r2 > 0, h, torch.full_like(h, c[0]))
+        psi[i] = (G * h).float()
+    del wz, wy, wx, r2, x, g, term, ri
+    fin = f[0]
+    out = torch.empty_like(fin)
+
+    def step():
+        fh = torch.fft.fftn(fin)
+        U = torch.fft.ifftn(fh[None] * psi, dim=(-3, -2, -1))
+        A = (torch.fft.fftn(U, dim=(-3, -2, -1)) * psi).sum(0)
+        out.copy_(torch.fft.ifftn(A * minv).real)
+
+    ms = timed(step, max(2, steps // 2))
+    ref = frec[0]
+    diff = float(torch.linalg.vector_norm(out - ref) / torch.linalg.vector_norm(ref))
+    # the same with the antipodal pairing (orientation i + N_o/2 = -n_i): one
+    # transform per pair each way, U_b = conj U_a written out as well
+    h = len(V) // 2
+    Ufull = torch.empty((len(V),) + tuple(dims), device=dev, dtype=torch.complex64)
+    out2 = torch.empty_like(fin)
+
+    def step_paired():
+        fh = torch.fft.fftn(fin)
+        Ua = torch.fft.ifftn(fh[None] * psi[:h], dim=(-3, -2, -1))
+        Ufull[:h] = Ua
+        Ufull[h:] = Ua.conj()
+        A = (torch.fft.fftn(Ufull[:h] + Ufull[h:].conj(), dim=(-3, -2, -1)) * psi[:h]).sum(0)
+        out2.copy_(torch.fft.ifftn(A * minv).real)
+
+    ms2 = timed(step_paired, max(2, steps // 2))
+    diff2 = float(torch.linalg.vector_norm(out2 - ref) / torch.linalg.vector_norm(ref))
+    nvox = int(math.prod(dims))
+    del psi, Ufull
+    torch.cuda.empty_cache()
+    return {"ms": ms, "value": nvox * len(V) / (ms / 1e3), "unit": UNIT,
+            "library": "cuFFT via torch.fft (comparison only)",
+            "recon_rel_l2_vs_ours": diff,
+            "paired_ms": ms2, "paired_value": nvox * len(V) / (ms2 / 1e3),
+            "paired_recon_rel_l2_vs_ours": diff2}
+
+
 # ---------------------------------------------------------------------------
 def run_ours(args):
     import numpy as np
@@ -397,6 +469,13 @@ def run_ours(args):
     ms_u = timed(lambda: os3d.os3d_upsilon(bank, f, 1.5, fu), args.steps)
     ops["upsilon_fused"] = {"ms": ms_u, "value": nvox * n_o / (ms_u / 1e3), "unit": UNIT,
                             "score_bytes_stored": 0}
+    # cuFFT comparison (not the product path): the straightforward batched form,
+    # f_hat = FFT(f), U = IFFT(f_hat psi_hat_i) for all i, then FFT of every U_i,
+    # multiply, orientation sum, x M^-1, IFFT; psi_hat_i stored (setup untimed)
+    os3d.os3d_forward(bank, f, U)          # our reconstruction, for the comparison's check
+    os3d.os3d_inverse(bank, U, frec)
+    ops["cufft_compare"] = _cufft_compare(os3d, bank, V, dims, w, f, frec, args.steps, timed)
+
     # linear diffusion: 42 orientations (the flows of Sec. 4.1 use N_o = 42), same grid
     V42 = os3d.os3d_icosa_orientations(1)
     bank42 = os3d.os3d_make_wavelets(dims, V42, os3d.os3d_default_params(L=w["L"]))
