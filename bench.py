@@ -275,7 +275,9 @@ def _cufft_compare(os3d, bank, V, dims, w, f, frec, steps, timed):
         A = (torch.fft.fftn(U, dim=(-3, -2, -1)) * psi).sum(0)
         out.copy_(torch.fft.ifftn(A * minv).real)
 
-    ms = timed(step, max(2, steps // 2))
+    # best of three rounds: its multi-GB temporaries go through torch's
+    # caching allocator, whose state varies from round to round
+    ms = min(timed(step, max(2, steps // 2)) for _ in range(3))
     ref = frec[0]
     diff = float(torch.linalg.vector_norm(out - ref) / torch.linalg.vector_norm(ref))
     # the same with the antipodal pairing (orientation i + N_o/2 = -n_i): one
@@ -292,7 +294,7 @@ def _cufft_compare(os3d, bank, V, dims, w, f, frec, steps, timed):
         A = (torch.fft.fftn(Ufull[:h] + Ufull[h:].conj(), dim=(-3, -2, -1)) * psi[:h]).sum(0)
         out2.copy_(torch.fft.ifftn(A * minv).real)
 
-    ms2 = timed(step_paired, max(2, steps // 2))
+    ms2 = min(timed(step_paired, max(2, steps // 2)) for _ in range(3))
     diff2 = float(torch.linalg.vector_norm(out2 - ref) / torch.linalg.vector_norm(ref))
     nvox = int(math.prod(dims))
     del psi, Ufull
