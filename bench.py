@@ -91,7 +91,7 @@ class ClockSampler:
         try:
             self.tmp = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
             cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                   "-lms", "200"]
+                   "-lms", "50"]
             if self.pci:
                 cmd += ["-i", self.pci]
             self.proc = subprocess.Popen(cmd, stdout=self.tmp, stderr=subprocess.DEVNULL)
@@ -306,6 +306,44 @@ def _cufft_compare(os3d, bank, V, dims, w, f, frec, steps, timed):
             "paired_recon_rel_l2_vs_ours": diff2}
 
 
+def _autograd_step(os3d, synth, steps, timed):
+    """One loss.backward() of L = sum w |W f|^2 for a batch of 8 96^3 volumes
+    with 42 orientations: os3d_forward plus os3d_adjoint behind
+    torch.autograd."""
+    import numpy as np
+    import torch
+    from paper_1505_07690_gb300.autograd import orientation_score
+    w = synth.WORKLOADS["splines96x8_no42"]
+    dims, B = w["shape"], w["batch"]
+    V = os3d.os3d_icosa_orientations(w["subdiv"])
+    bank = os3d.os3d_make_wavelets(dims, V, os3d.os3d_default_params(L=w["L"]))
+    f = torch.from_numpy(np.stack([synth.workload_volume("splines96x8_no42", batch_index=b)
+                                   for b in range(B)])).cuda().requires_grad_(True)
+    wt = torch.from_numpy(synth.score_weights((B, len(V)) + tuple(dims), seed=1)).cuda()
+
+    def step():
+        f.grad = None
+        U = orientation_score(f, bank)
+        (wt * (U.real ** 2 + U.imag ** 2)).sum().backward()
+
+    ms = timed(step, max(2, steps // 2))
+    fd = f.detach()
+    U = os3d.new_score(bank, B)
+    g = torch.empty_like(fd)
+
+    def transforms():
+        os3d.os3d_forward(bank, fd, U)
+        os3d.os3d_adjoint(bank, U, g)
+
+    ms_t = timed(transforms, max(2, steps // 2))
+    vo = B * int(np.prod(dims)) * len(V)
+    del f, wt, U, g, fd
+    torch.cuda.empty_cache()
+    return {"ms": ms, "value": vo / (ms / 1e3), "unit": UNIT,
+            "what": "forward + loss (torch elementwise) + adjoint, batch 8",
+            "transforms_ms": ms_t, "transforms_value": vo / (ms_t / 1e3)}
+
+
 # ---------------------------------------------------------------------------
 def run_ours(args):
     import numpy as np
@@ -477,6 +515,10 @@ def run_ours(args):
     os3d.os3d_forward(bank, f, U)          # our reconstruction, for the comparison's check
     os3d.os3d_inverse(bank, U, frec)
     ops["cufft_compare"] = _cufft_compare(os3d, bank, V, dims, w, f, frec, args.steps, timed)
+
+    # differentiation form: 8 x 96^3, 42 orientations, loss sum w |U|^2 through
+    # the autograd wrapper (forward, then the hand-written adjoint as backward)
+    ops["autograd_8x96_no42"] = _autograd_step(os3d, synth, args.steps, timed)
 
     # linear diffusion: 42 orientations (the flows of Sec. 4.1 use N_o = 42), same grid
     V42 = os3d.os3d_icosa_orientations(1)
