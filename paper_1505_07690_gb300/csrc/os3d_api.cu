@@ -26,7 +26,7 @@ namespace os3d {
 OS3D_DECL_Z(16) OS3D_DECL_Z(32) OS3D_DECL_Z(48) OS3D_DECL_Z(64) OS3D_DECL_Z(96)
 OS3D_DECL_Z(128) OS3D_DECL_Z(160) OS3D_DECL_Z(256)
 OS3D_DECL_XY(16, 16) OS3D_DECL_XY(32, 32) OS3D_DECL_XY(48, 48) OS3D_DECL_XY(64, 64)
-OS3D_DECL_XY(96, 96) OS3D_DECL_XY(128, 128)
+OS3D_DECL_XY(96, 96) OS3D_DECL_XY(128, 128) OS3D_DECL_XY(256, 256)
 #define OS3D_DECL_PN(N)                                                                   \
   cudaError_t launch_pencil_##N(int, int, int, const PassArgs&, const PencilGeom&, long long, \
                                 int, cudaStream_t);
@@ -53,8 +53,11 @@ bool z_supported(int nz) {
          nz == 256;
 }
 bool xy_supported(int ny, int nx) {
-  return ny == nx && (nx == 16 || nx == 32 || nx == 48 || nx == 64 || nx == 96 || nx == 128);
+  return ny == nx &&
+         (nx == 16 || nx == 32 || nx == 48 || nx == 64 || nx == 96 || nx == 128 || nx == 256);
 }
+// planes the fused soft-threshold plane pass holds (2-CTA clusters)
+bool soft_plane_supported(int ny, int nx) { return xy_supported(ny, nx) && nx <= 128; }
 cudaError_t launch_z(int nz, int mode, int ev, const PassArgs& a, int tiles, cudaStream_t s) {
   switch (nz) {
     case 16: return launch_z_16(mode, ev, a, tiles, s);
@@ -77,6 +80,7 @@ cudaError_t launch_xy(int ny, int nx, int mode, int ub, const PassArgs& a, cudaS
     case 64: return launch_xy_64_64(mode, ub, a, s);
     case 96: return launch_xy_96_96(mode, ub, a, s);
     case 128: return launch_xy_128_128(mode, ub, a, s);
+    case 256: return launch_xy_256_256(mode, ub, a, s);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -826,7 +830,7 @@ cudaError_t launch_plane(const os3d_bank* b, int mode, int ub, const PassArgs& a
 // IDFT_y, IDFT_x, the soft threshold, DFT_x, DFT_y.
 cudaError_t launch_plane_soft(const os3d_bank* b, const PassArgs& a, cudaStream_t s) {
   const int nz = b->dims[0], ny = b->dims[1], nx = b->dims[2];
-  if (xy_supported(ny, nx)) return launch_xy(ny, nx, XY_SOFT, 0, a, s);
+  if (soft_plane_supported(ny, nx)) return launch_xy(ny, nx, XY_SOFT, 0, a, s);
   const long long P = (long long)ny * nx;
   const PencilGeom gx{ny, P, nx, 1};
   const PencilGeom gy{nx, P, 1, nx};
@@ -978,6 +982,8 @@ os3d_status upsilon_impl(const os3d_bank* b, const float* f, int batch, float* f
       set_slots(b, za, v, s0, ns);
       za.in = w.fh;
       za.out = w.T[k];
+      // the pencil passes of the score-domain step read every column of T
+      za.disc = soft_plane_supported(ny, nx) ? 1 : 0;
       OS3D_CK(counted_launch(OS3D_KIND_Z_FWD_SCORE, st2,
                              [&] { return launch_z(nz, Z_FWD_SCORE, b->ev, za, tiles, st2); }));
       PassArgs xa = za;

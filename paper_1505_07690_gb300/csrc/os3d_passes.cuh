@@ -298,20 +298,25 @@ z_kernel(const __grid_constant__ PassArgs a) {
 }
 
 // ----------------------------------------------------------------------------
-// xy-pass on a 2-CTA cluster. CTA h holds rows [h NY/2, (h+1) NY/2) of a
-// z-plane for the x direction and columns [h NX/2, (h+1) NX/2) for the y
-// direction; the x step-2 outputs go straight into the owner's y-layout
-// buffer (local or distributed shared memory). Half a plane (74 KB at 128^2)
-// lets two CTAs share an SM, so one CTA's loads overlap the other's DFTs.
+// xy-pass on a cluster of NS CTAs (2, or 8 for 256^2 planes). CTA h holds rows
+// [h NY/NS, (h+1) NY/NS) of a z-plane for the x direction and columns
+// [h NX/NS, (h+1) NX/NS) for the y direction; the x step-2 outputs go straight
+// into the owner's y-layout buffer (local or distributed shared memory). Half a
+// plane (74 KB at 128^2; an eighth, 84 KB, at 256^2) lets two CTAs share an
+// SM, so one CTA's loads overlap the other's DFTs.
 // Shared layout: x layout row pitch NX + 8 (rows alternate 64-byte halves of
 // the bank space) with an XOR swizzle inside each group of R2x columns; y
 // layout row pitch NX/2 + 8. All accesses of the 128^2 plan are
 // bank-conflict-free. Work units: (plane, slot) for the score modes, planes
 // for the real modes; clusters loop over units.
 // ----------------------------------------------------------------------------
-template <int NY, int NX>
+// CTAs per plane (NS) and the largest thread count per CTA
+template <int NY, int NX> struct XYSplit { static constexpr int NS = 2, NTMAX = 256; };
+template <> struct XYSplit<256, 256> { static constexpr int NS = 8, NTMAX = 256; };
+
+template <int NY, int NX, int NS = XYSplit<NY, NX>::NS, int NTMAX = XYSplit<NY, NX>::NTMAX>
 struct XYCfg {
-  static constexpr int NYH = NY / 2, NXH = NX / 2;
+  static constexpr int NYH = NY / NS, NXH = NX / NS;   // rows / columns of one CTA
   static constexpr int R1x = Plan<NX>::R1, R2x = Plan<NX>::R2;
   static constexpr int R1y = Plan<NY>::R1, R2y = Plan<NY>::R2;
   static_assert((R2x & (R2x - 1)) == 0, "R2x must be a power of two");
@@ -320,7 +325,7 @@ struct XYCfg {
            nt % R2y == 0 && NXH % (nt / R2y) == 0 && (NXH * R1y) % nt == 0;
   }
   static constexpr int pick() {
-    for (int nt = 256; nt >= 32; nt -= 32)
+    for (int nt = NTMAX; nt >= 32; nt -= 32)
       if (ok(nt)) return nt;
     return 0;
   }
@@ -366,9 +371,10 @@ __device__ __forceinline__ float2 load_u(const void* base, long long i) {
 }
 
 template <int NY, int NX, int MODE, int UBF16>
-__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(XYCfg<NY, NX>::NT, 2)
+__global__ void __cluster_dims__(XYSplit<NY, NX>::NS, 1, 1) __launch_bounds__(XYCfg<NY, NX>::NT, 2)
 xy_kernel(const __grid_constant__ PassArgs a) {
   using C = XYCfg<NY, NX>;
+  constexpr int NS = XYSplit<NY, NX>::NS;
   constexpr int R1x = C::R1x, R2x = C::R2x, R1y = C::R1y, R2y = C::R2y;
   constexpr int NT = C::NT, NYH = C::NYH, NXH = C::NXH;
   constexpr int DIR = (MODE == XY_FWD_REAL || MODE == XY_INV_SCORE) ? -1 : +1;
@@ -380,9 +386,11 @@ xy_kernel(const __grid_constant__ PassArgs a) {
 
   const int t = threadIdx.x;
   const int h = (int)cluster_rank();
-  const unsigned peer_base = map_cluster_rank(smem_addr(work), (unsigned)(h ^ 1));
+  unsigned peer_base[NS];   // the work buffer of every CTA of the cluster
+#pragma unroll
+  for (int q = 0; q < NS; ++q) peer_base[q] = map_cluster_rank(smem_addr(work), (unsigned)q);
   const long long P = (long long)NY * NX;
-  const int cl = blockIdx.x >> 1, ncl = gridDim.x >> 1;
+  const int cl = blockIdx.x / NS, ncl = gridDim.x / NS;
   const int nsl = (MODE == XY_FWD_SCORE || MODE == XY_INV_SCORE) ? a.nslots : 1;
   const int nunits = a.nz * nsl;
 
@@ -473,10 +481,10 @@ xy_kernel(const __grid_constant__ PassArgs a) {
 #pragma unroll
         for (int k2 = 0; k2 < R2x; ++k2) {
           const int c = k1 + R1x * k2;
-          const int owner = (NXH % R1x == 0) ? (k2 >= NXH / R1x) : (c >= NXH);
+          const int owner = (NXH % R1x == 0) ? (k2 / (NXH / R1x)) : (c / NXH);
           const int idx = row + c - owner * NXH;
           if (owner == h) work[idx] = w[j][k2];
-          else st_cluster_f2(peer_base + 8u * (unsigned)idx, w[j][k2]);
+          else st_cluster_f2(peer_base[owner] + 8u * (unsigned)idx, w[j][k2]);
         }
       }
       cluster_sync_acqrel();   // this CTA's y-layout buffer is complete
@@ -557,9 +565,9 @@ xy_kernel(const __grid_constant__ PassArgs a) {
 // T_s.
 // ----------------------------------------------------------------------------
 template <int NY, int NX>
-__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(XYCfg<NY, NX>::NT, 2)
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(XYCfg<NY, NX, 2, 256>::NT, 2)
 xy_soft_kernel(const __grid_constant__ PassArgs a) {
-  using C = XYCfg<NY, NX>;
+  using C = XYCfg<NY, NX, 2, 256>;
   constexpr int R1x = C::R1x, R2x = C::R2x, R1y = C::R1y, R2y = C::R2y;
   constexpr int NT = C::NT, NYH = C::NYH, NXH = C::NXH;
 
@@ -763,7 +771,7 @@ xy_soft_kernel(const __grid_constant__ PassArgs a) {
 
 template <int NY, int NX>
 cudaError_t launch_xy_soft_one(const PassArgs& a, cudaStream_t s) {
-  using C = XYCfg<NY, NX>;
+  using C = XYCfg<NY, NX, 2, 256>;
   auto k = xy_soft_kernel<NY, NX>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)C::smem_bytes);
@@ -811,9 +819,10 @@ cudaError_t launch_xy_one(const PassArgs& a, cudaStream_t s) {
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   const int nsl = (MODE == XY_FWD_SCORE || MODE == XY_INV_SCORE) ? a.nslots : 1;
-  // two CTAs per SM, two per cluster: as many clusters as SMs, looping over units
-  const int clusters = std::max(1, std::min(a.nz * nsl, nsm));
-  k<<<2 * clusters, C::NT, C::smem_bytes, s>>>(a);
+  // two CTAs per SM, NS per cluster: 2 nsm / NS clusters, looping over units
+  constexpr int NS = XYSplit<NY, NX>::NS;
+  const int clusters = std::max(1, std::min(a.nz * nsl, 2 * nsm / NS));
+  k<<<NS * clusters, C::NT, C::smem_bytes, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -828,7 +837,9 @@ cudaError_t launch_xy_n(int mode, int ub, const PassArgs& a, cudaStream_t s) {
     case XY_INV_SCORE:
       return ub ? launch_xy_one<NY, NX, XY_INV_SCORE, 1>(a, s)
                 : launch_xy_one<NY, NX, XY_INV_SCORE, 0>(a, s);
-    case XY_SOFT: return launch_xy_soft_one<NY, NX>(a, s);
+    case XY_SOFT:
+      if constexpr (NX <= 128) return launch_xy_soft_one<NY, NX>(a, s);
+      else return cudaErrorInvalidValue;
     default: return cudaErrorInvalidValue;
   }
 }

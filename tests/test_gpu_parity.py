@@ -282,3 +282,15 @@ def test_batch_zero_is_rejected(M):
     L = M.lib()
     assert L.os3d_forward(bank.handle, ctypes.c_void_p(1), 0, ctypes.c_void_p(1), 0, None, None) == 1
     assert L.os3d_inverse(bank.handle, ctypes.c_void_p(1), 0, 0, ctypes.c_void_p(1), None, None) == 1
+
+
+def test_plane_pass_256_squared(M):
+    """256^2 planes take the plane pass on 8-CTA clusters (an eighth of a plane
+    per CTA); 32 x 256 x 256 keeps the oracle fast."""
+    dims = (32, 256, 256)
+    f = synth.straight_tubes(dims, 3, seed=54, noise=0.1)
+    _check_forward_inverse(M, dims, f, subdiv=0, L=12, block_slots=4)
+    # Upsilon on this grid: the score-domain step takes the pencil passes
+    bank, ob = _pair(M, dims, subdiv=0, L=12, block_slots=4)
+    fu = _to_np(M.os3d_upsilon(bank, _cuda(f), 1.5))
+    assert rel(fu, O.upsilon(f, ob, 1.5)) <= TOL
