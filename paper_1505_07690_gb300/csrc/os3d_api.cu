@@ -637,6 +637,8 @@ os3d_status os3d_make_wavelets(const int dims[3], const double* orient, int n_o,
       b->ev = L <= 16 ? 0 : 1;
       for (int k = 0; k < 13; ++k) b->h.e[k] = k < (int)e.size() ? (float)e[k] : 0.f;
       for (int k = 0; k < 12; ++k) b->h.o[k] = k < (int)o.size() ? (float)o[k] : 0.f;
+      for (int k = 0; k < 13; ++k) b->h.e2[k] = make_float2(b->h.e[k], b->h.e[k]);
+      for (int k = 0; k < 12; ++k) b->h.o2[k] = make_float2(b->h.o[k], b->h.o[k]);
     }
   }
 

@@ -19,6 +19,7 @@ struct HEval {
   float o[12];
   float a[kMaxL + 1];
   float c0;   // value used at w = 0: the spherical mean of h
+  float2 e2[13], o2[12];   // (e_k, e_k) and (o_k, o_k): operands of two-lane FMAs
 };
 
 // z-passes (DFT along z of 16-wide pencil tiles):

@@ -67,6 +67,25 @@ __device__ __forceinline__ float eval_h(const HEval& h, float t) {
   }
 }
 
+// h at the two points t.x and t.y at once (two-lane FMAs for the split forms).
+template <int EV>
+__device__ __forceinline__ float2 eval_h2(const HEval& h, float2 t) {
+  if constexpr (EV < 2) {
+    constexpr int NE = EV == 0 ? 9 : 13;
+    constexpr int NO = NE - 1;
+    const float2 v = fma2(t, t, make_float2(-0.5f, -0.5f));
+    float2 e = h.e2[NE - 1];
+#pragma unroll
+    for (int k = NE - 2; k >= 0; --k) e = fma2k(e, v, h.e2[k]);
+    float2 o = h.o2[NO - 1];
+#pragma unroll
+    for (int k = NO - 2; k >= 0; --k) o = fma2k(o, v, h.o2[k]);
+    return fma2(t, o, e);
+  } else {
+    return make_float2(eval_h<EV>(h, t.x), eval_h<EV>(h, t.y));
+  }
+}
+
 template <int UBF16>
 __device__ __forceinline__ void store_u(void* base, long long i, float2 v) {
   if constexpr (UBF16) {
@@ -199,25 +218,28 @@ z_kernel(const __grid_constant__ PassArgs a) {
       const int z = n2 + R2 * n1;
       keep[z * TW + xl] = reinterpret_cast<const float2*>(a.in)[(long long)z * plane + col];
     }
-    float ur[R1], rr[R1];   // w_z / |w| and 1 / |w| at the step-1 frequencies
+    static_assert(R1 % 2 == 0, "points are evaluated in pairs");
+    float2 ur[R1 / 2], rr[R1 / 2];   // w_z / |w| and 1 / |w| at the step-1 frequencies (pairs)
 #pragma unroll
     for (int n1 = 0; n1 < R1; ++n1) {
       const float wz = float(signed_index(n2 + R2 * n1, NZ)) * a.wz;
       const float r2 = fmaf(wz, wz, rxy2);
       const float ri = r2 > 0.f ? rsqrtf(r2) : 0.f;
-      ur[n1] = wz * ri;
-      rr[n1] = ri;
+      (n1 % 2 ? ur[n1 / 2].y : ur[n1 / 2].x) = wz * ri;
+      (n1 % 2 ? rr[n1 / 2].y : rr[n1 / 2].x) = ri;
     }
     __syncthreads();
     for (int s = 0; s < a.nslots; ++s) {
       const float dxy = fmaf(wx, a.nvec[s][0], wy * a.nvec[s][1]);
       const float nz = a.nvec[s][2];
+      const float2 dxy2 = make_float2(dxy, dxy), nz2 = make_float2(nz, nz);
       float2 v[R1];
 #pragma unroll
-      for (int n1 = 0; n1 < R1; ++n1) {
-        float hv = eval_h<EV>(a.h, fmaf(rr[n1], dxy, ur[n1] * nz));
-        if (n1 == 0 && n2 == 0 && dc_col) hv = a.h.c0;
-        v[n1] = cscale(keep[(n2 + R2 * n1) * TW + xl], hv);
+      for (int m = 0; m < R1 / 2; ++m) {
+        float2 hv = eval_h2<EV>(a.h, fma2(rr[m], dxy2, mul2(ur[m], nz2)));
+        if (m == 0 && n2 == 0 && dc_col) hv.x = a.h.c0;
+        v[2 * m] = cscale(keep[(n2 + R2 * 2 * m) * TW + xl], hv.x);
+        v[2 * m + 1] = cscale(keep[(n2 + R2 * (2 * m + 1)) * TW + xl], hv.y);
       }
       step1(v);
       __syncthreads();
@@ -234,7 +256,8 @@ z_kernel(const __grid_constant__ PassArgs a) {
       __syncthreads();
     }
   } else {  // Z_INV_SCORE: for each slot T_s -> DFT_z -> x h, summed into A
-    float ur[J3 * R2], rr[J3 * R2];   // at the step-2 output frequencies
+    static_assert(R2 % 2 == 0, "points are evaluated in pairs");
+    float2 ur[J3 * R2 / 2], rr[J3 * R2 / 2];   // at the step-2 output frequencies (pairs)
 #pragma unroll
     for (int j = 0; j < J3; ++j) {
 #pragma unroll
@@ -243,8 +266,9 @@ z_kernel(const __grid_constant__ PassArgs a) {
         const float wz = float(signed_index(kz, NZ)) * a.wz;
         const float r2 = fmaf(wz, wz, rxy2);
         const float ri = r2 > 0.f ? rsqrtf(r2) : 0.f;
-        ur[j * R2 + k2] = wz * ri;
-        rr[j * R2 + k2] = ri;
+        const int p = j * R2 + k2;
+        (p % 2 ? ur[p / 2].y : ur[p / 2].x) = wz * ri;
+        (p % 2 ? rr[p / 2].y : rr[p / 2].x) = ri;
       }
     }
 #pragma unroll
@@ -268,19 +292,23 @@ z_kernel(const __grid_constant__ PassArgs a) {
       __syncthreads();
       const float dxy = fmaf(wx, a.nvec[s][0], wy * a.nvec[s][1]);
       const float nz = a.nvec[s][2];
+      const float2 dxy2 = make_float2(dxy, dxy), nz2 = make_float2(nz, nz);
 #pragma unroll
       for (int j = 0; j < J3; ++j) {
         if (R1 % R2 != 0 && n2 + R2 * j >= R1) break;
         float2 w[R2];
         step2(j, w);
 #pragma unroll
-        for (int k2 = 0; k2 < R2; ++k2) {
-          const int p = j * R2 + k2;
-          float hv = eval_h<EV>(a.h, fmaf(rr[p], dxy, ur[p] * nz));
-          if (p == 0 && n2 == 0 && dc_col) hv = a.h.c0;
-          float2& d = keep[(n2 + R2 * j + R1 * k2) * TW + xl];
-          d.x = fmaf(hv, w[k2].x, d.x);
-          d.y = fmaf(hv, w[k2].y, d.y);
+        for (int k2 = 0; k2 < R2; k2 += 2) {
+          const int p = (j * R2 + k2) / 2;
+          float2 hv = eval_h2<EV>(a.h, fma2(rr[p], dxy2, mul2(ur[p], nz2)));
+          if (p == 0 && n2 == 0 && dc_col) hv.x = a.h.c0;
+          float2& d0 = keep[(n2 + R2 * j + R1 * k2) * TW + xl];
+          d0.x = fmaf(hv.x, w[k2].x, d0.x);
+          d0.y = fmaf(hv.x, w[k2].y, d0.y);
+          float2& d1 = keep[(n2 + R2 * j + R1 * (k2 + 1)) * TW + xl];
+          d1.x = fmaf(hv.y, w[k2 + 1].x, d1.x);
+          d1.y = fmaf(hv.y, w[k2 + 1].y, d1.y);
         }
       }
       __syncthreads();
