@@ -118,11 +118,11 @@ enhance_kernel(const __grid_constant__ EnhanceArgs a) {
     __syncthreads();
     // ---- K Strang steps: V <- F^2 (E V) (F at the last step)
     for (int s = 0; s < a.steps; ++s) {
-      float acc[4][8];
+      float2 acc[4][4];   // pairs of adjacent frequencies (two-lane FMAs)
 #pragma unroll
       for (int r = 0; r < 4; ++r)
 #pragma unroll
-        for (int c = 0; c < 8; ++c) acc[r][c] = 0.f;
+        for (int c = 0; c < 4; ++c) acc[r][c] = make_float2(0.f, 0.f);
       // rows j = 4 jq .. 4 jq + 3 share the swizzle of their quad jq
 #pragma unroll 1
       for (int jq = 0; jq < NP / 4; ++jq) {
@@ -134,11 +134,14 @@ enhance_kernel(const __grid_constant__ EnhanceArgs a) {
           const float4 v0 = *reinterpret_cast<const float4*>(V + o0 + jj * kTV);
           const float4 v1 = *reinterpret_cast<const float4*>(V + o1 + jj * kTV);
           const float ev[4] = {e.x, e.y, e.z, e.w};
-          const float vv[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+          const float2 vv[4] = {make_float2(v0.x, v0.y), make_float2(v0.z, v0.w),
+                                make_float2(v1.x, v1.y), make_float2(v1.z, v1.w)};
 #pragma unroll
-          for (int r = 0; r < 4; ++r)
+          for (int r = 0; r < 4; ++r) {
+            const float2 er = make_float2(ev[r], ev[r]);
 #pragma unroll
-            for (int c = 0; c < 8; ++c) acc[r][c] = fmaf(ev[r], vv[c], acc[r][c]);
+            for (int c = 0; c < 4; ++c) acc[r][c] = fma2(er, vv[c], acc[r][c]);
+          }
         }
       }
       const bool last = s == a.steps - 1;
@@ -150,11 +153,13 @@ enhance_kernel(const __grid_constant__ EnhanceArgs a) {
         for (int hh = 0; hh < 2; ++hh) {
           const int off = vofs(i, 8 * vg + 4 * hh);
           const float4 f = *reinterpret_cast<const float4*>(F + off);
-          const float w0 = last ? f.x : f.x * f.x, w1 = last ? f.y : f.y * f.y;
-          const float w2 = last ? f.z : f.z * f.z, w3 = last ? f.w : f.w * f.w;
-          *reinterpret_cast<float4*>(V + off) =
-              make_float4(acc[r][4 * hh] * w0, acc[r][4 * hh + 1] * w1, acc[r][4 * hh + 2] * w2,
-                          acc[r][4 * hh + 3] * w3);
+          float2 w01 = make_float2(f.x, f.y), w23 = make_float2(f.z, f.w);
+          if (!last) {
+            w01 = mul2(w01, w01);
+            w23 = mul2(w23, w23);
+          }
+          const float2 p01 = mul2(acc[r][2 * hh], w01), p23 = mul2(acc[r][2 * hh + 1], w23);
+          *reinterpret_cast<float4*>(V + off) = make_float4(p01.x, p01.y, p23.x, p23.y);
         }
       }
       __syncthreads();
