@@ -72,7 +72,7 @@ typedef struct {
   double eps;       /* clamp M -> max(M, eps) of the inverse, eps > 0                */
   int fit_mode;     /* 1: least squares on the order-15 icosahedral tessellation
                        (the paper's pseudo-inverse); 0: L2 projection (Gauss-Legendre) */
-  int block_slots;  /* orientation pairs per launch block, 0 = automatic (8), else 1..8 */
+  int block_slots;  /* orientation pairs per launch block, 0 = automatic (11), else 1..12 */
   int overlap;      /* 1: consecutive blocks alternate between two internal streams of the
                        bank (forked from and joined to the caller's stream); 0: every launch
                        on the caller's stream (for callers running many transforms at once) */

@@ -522,10 +522,11 @@ os3d_status os3d_make_wavelets(const int dims[3], const double* orient, int n_o,
   if (p.block_slots > 0) {
     b->block_slots = p.block_slots;
   } else {
-    // the largest block: fewer, longer launches; with the two side streams
-    // the intermediates of consecutive blocks overlap in time (measured best
-    // at 128^3 x 162: 8 pairs per block, 2.55 ms vs 2.69 ms at 3)
-    b->block_slots = kMaxSlots;
+    // long blocks: fewer, longer launches; with the two side streams the
+    // intermediates of consecutive blocks overlap in time (measured at
+    // 128^3 x 162, forward + inverse: 2.26, 2.24, 2.22, 2.24 ms for blocks of
+    // 8, 10, 11, 12 pairs; 2.69 ms at 3)
+    b->block_slots = kAutoSlots;
   }
   b->block_slots = std::min(b->block_slots, nslots);
   // f_hat, two partial orientation sums, one per-volume intermediate and two

@@ -7,7 +7,8 @@
 
 namespace os3d {
 
-constexpr int kMaxSlots = 8;    // orientation slots per launch block
+constexpr int kMaxSlots = 12;   // orientation slots per launch block
+constexpr int kAutoSlots = 11;  // block size when the caller leaves it to the library
 constexpr int kMaxL = 32;       // maximal Legendre degree
 constexpr int kTileX = 16;      // x-width of a z-pencil tile
 

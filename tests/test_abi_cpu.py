@@ -99,7 +99,7 @@ def test_argument_errors_before_any_launch(L):
                                 ctypes.byref(p), None, ctypes.byref(h)) == 1
     # parameters out of range
     for field, val in (("L", 33), ("eps", 0.0), ("gamma", 1.0), ("k", 9), ("fit_mode", 2),
-                       ("s_theta", -1.0), ("block_slots", 9), ("profile", 2)):
+                       ("s_theta", -1.0), ("block_slots", 13), ("profile", 2)):
         q = os3d.os3d_default_params(**{field: val})
         assert L.os3d_make_wavelets(dims, Vp, 42, ctypes.byref(q), None, ctypes.byref(h)) == 1, field
     # grid without a compiled plan
