@@ -102,6 +102,14 @@ def test_forward_inverse_sizes(M, dims, subdiv, L, bs):
     _check_forward_inverse(M, dims, f, subdiv=subdiv, L=L, block_slots=bs)
 
 
+@pytest.mark.parametrize("bs,subdiv", [(11, 1), (12, 1), (11, 2), (12, 2)])
+def test_long_blocks(M, bs, subdiv):
+    """Blocks of 11 (the automatic size) and 12 pairs (the limit): 21 pairs
+    split 11 + 10 and 12 + 9, 81 pairs 7 x 11 + 4 and 6 x 12 + 9."""
+    f = synth.straight_tubes((32, 32, 32), 3, seed=6, noise=0.1)
+    _check_forward_inverse(M, (32, 32, 32), f, subdiv=subdiv, L=12, block_slots=bs)
+
+
 def test_unpaired_orientations_and_ragged_blocks(M):
     """Orientations without antipodes take the single-orientation path; 21
     slots in blocks of 4 leave a ragged last block."""
