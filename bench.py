@@ -539,9 +539,9 @@ def run_ours(args):
     inball = int(np.count_nonzero(wz ** 2 + wy ** 2 + wx ** 2 < np.pi ** 2))
     no42 = len(V42)
     # the kernel integrates half of the ball (the factor is even in w for an
-    # antipodally closed set) with the orientation count padded to a multiple of 4
-    npad = (no42 + 3) // 4 * 4
-    flops = (inball + 1) // 2 * (dif.steps * 2 * npad * npad + 2 * no42 * 34 + npad * 12)
+    # antipodally closed set); counted with the real orientation count (the
+    # kernel pads it to a multiple of 8 and executes more)
+    flops = (inball + 1) // 2 * (dif.steps * 2 * no42 * no42 + 2 * no42 * 34 + no42 * 12)
     k_ms = pe[1] / max(pe[0], 1)
     fp32_peak = nsm * 128 * 2 * (clk["sm_mhz"] if clk else 2070.0) * 1e6 / 1e12
     ops["enhance_linear"] = {

@@ -1138,7 +1138,7 @@ os3d_status os3d_enhance_linear(const os3d_bank* b, const float* f, int batch, f
   e.D33 = float(d->D33);
   for (int i = 0; i < b->n_o; ++i) {
     for (int q = 0; q < 3; ++q) e.nvec[i][q] = float(b->orient[3 * i + q]);
-    for (int j = 0; j < b->n_o; ++j) e.E[i * kMaxOrientE + j] = float(E[(size_t)i * b->n_o + j]);
+    for (int j = 0; j < b->n_o; ++j) e.Et[j * kEStride + i] = float(E[(size_t)i * b->n_o + j]);
   }
   e.h = b->h;
   cudaStream_t s = (cudaStream_t)stream;

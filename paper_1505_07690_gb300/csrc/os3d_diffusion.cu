@@ -25,13 +25,14 @@ namespace {
 
 constexpr double kPiH = 3.141592653589793238462643383279502884;
 
-// One CTA per tile of TV = 128 listed frequencies, 4 NP threads; NP = the
-// orientation count padded to a multiple of 4. Per Strang step each thread
-// accumulates a 4 (orientations) x 8 (frequencies) tile of E V from shared
-// memory, so every propagator value it loads feeds 8 FMAs; the tile is written
-// back in place after a barrier. Vectors are stored [orientation][frequency]
-// with the float4 columns XOR-swizzled by the orientation quad, so that the
-// tile writes of the lanes (consecutive quads) fall on distinct banks.
+// One CTA per tile of TV = 128 listed frequencies, NP / 8 warps; NP = the
+// orientation count padded to a multiple of 8. Per Strang step warp w
+// accumulates rows 8w .. 8w+7 of E V, each lane 4 consecutive frequencies:
+// per propagator column j a lane reads its 4 vector entries with one 16-byte
+// shared load and the 8 propagator entries, the same for the whole warp, as
+// four 8-byte shared broadcasts, and issues 16 two-lane FMAs over pairs of
+// adjacent rows. The tile is written back in place after a barrier.
+// Vectors are stored [orientation][frequency], rows of TV floats.
 constexpr int kTV = 128;
 
 template <int NP>
@@ -40,30 +41,24 @@ constexpr size_t enhance_smem() {
          sizeof(int) * 2 * kTV;
 }
 
-// offset of element (i, q) of a [NP][kTV] vector array
-__device__ __forceinline__ int vofs(int i, int q) {
-  return i * kTV + ((((q >> 2) ^ (i >> 2)) & 7) | ((q >> 2) & ~7)) * 4 + (q & 3);
-}
-
 template <int NP, int EV>
 __global__ void __launch_bounds__(4 * NP)
 enhance_kernel(const __grid_constant__ EnhanceArgs a) {
-  constexpr int NT = 4 * NP, TV = kTV, NQ = NP / 4;
+  static_assert(NP % 8 == 0 && NP <= kEStride, "8 propagator rows per warp");
+  constexpr int NT = 4 * NP, TV = kTV;
   extern __shared__ __align__(16) float esm[];
-  float* Et = esm;                       // Et[j * NP + i] = E[i][j]
-  float* V = Et + NP * NP;               // [i][q] (swizzled, see vofs)
+  float* Es = esm;                       // Es[j * NP + i] = E[i][j]
+  float* V = Es + NP * NP;               // [i][q]
   float* F = V + NP * TV;                // half-step factors exp(-dt/2 r_i)
   float* nv = F + NP * TV;               // orientations (3 per row)
   float* geo = nv + 3 * NP;              // wx, wy, wz, 1/|w|, |w|^2 per slot
   int* vox = reinterpret_cast<int*>(geo + 5 * TV);
   int* mvox = vox + TV;
   const int t = threadIdx.x;
-  const int ig = t % NQ, vg = t / NQ;
+  const int i0 = 8 * (t >> 5), q0 = 4 * (t & 31);
+  const int nj = (a.n_o + 3) & ~3;       // columns j >= n_o of E are zero
 
-  for (int q = t; q < NP * NP; q += NT) {
-    const int j = q / NP, i = q % NP;
-    Et[q] = (i < a.n_o && j < a.n_o) ? a.E[i * kMaxOrientE + j] : 0.f;
-  }
+  for (int q = t; q < NP * NP; q += NT) Es[q] = a.Et[(q / NP) * kEStride + q % NP];
   for (int q = t; q < 3 * NP; q += NT) nv[q] = (q / 3 < a.n_o) ? a.nvec[q / 3][q % 3] : 0.f;
 
   const int ntiles = (a.n_in + TV - 1) / TV;
@@ -112,33 +107,28 @@ enhance_kernel(const __grid_constant__ EnhanceArgs a) {
         f = expf(-a.half_dt * fmaf(a.D11, r2 - tau * tau, a.D33 * tau * tau));
         if (i < a.n_o) hv = r2 > 0.f ? eval_h<EV>(a.h, tau * geo[3 * TV + q]) : a.h.c0;
       }
-      F[vofs(i, q)] = f;
-      V[vofs(i, q)] = hv * f;
+      F[i * TV + q] = f;
+      V[i * TV + q] = hv * f;
     }
     __syncthreads();
     // ---- K Strang steps: V <- F^2 (E V) (F at the last step)
     for (int s = 0; s < a.steps; ++s) {
-      float2 acc[4][4];   // pairs of adjacent frequencies (two-lane FMAs)
+      float2 acc[4][4];   // acc[r][c]: rows i0 + 2r, i0 + 2r + 1 at frequency q0 + c
 #pragma unroll
       for (int r = 0; r < 4; ++r)
 #pragma unroll
         for (int c = 0; c < 4; ++c) acc[r][c] = make_float2(0.f, 0.f);
-      // rows j = 4 jq .. 4 jq + 3 share the swizzle of their quad jq
 #pragma unroll 1
-      for (int jq = 0; jq < NP / 4; ++jq) {
-        const int o0 = vofs(4 * jq, 8 * vg), o1 = vofs(4 * jq, 8 * vg + 4);
-        const float* er = Et + 4 * jq * NP + 4 * ig;
+      for (int j0 = 0; j0 < nj; j0 += 4) {
 #pragma unroll
         for (int jj = 0; jj < 4; ++jj) {
-          const float4 e = *reinterpret_cast<const float4*>(er + jj * NP);
-          const float4 v0 = *reinterpret_cast<const float4*>(V + o0 + jj * kTV);
-          const float4 v1 = *reinterpret_cast<const float4*>(V + o1 + jj * kTV);
-          const float ev[4] = {e.x, e.y, e.z, e.w};
-          const float2 vv[4] = {make_float2(v0.x, v0.y), make_float2(v0.z, v0.w),
-                                make_float2(v1.x, v1.y), make_float2(v1.z, v1.w)};
+          const int j = j0 + jj;
+          const float4 v = *reinterpret_cast<const float4*>(V + j * TV + q0);
+          const float2 vv[4] = {make_float2(v.x, v.x), make_float2(v.y, v.y),
+                                make_float2(v.z, v.z), make_float2(v.w, v.w)};
 #pragma unroll
           for (int r = 0; r < 4; ++r) {
-            const float2 er = make_float2(ev[r], ev[r]);
+            const float2 er = *reinterpret_cast<const float2*>(Es + j * NP + i0 + 2 * r);
 #pragma unroll
             for (int c = 0; c < 4; ++c) acc[r][c] = fma2(er, vv[c], acc[r][c]);
           }
@@ -148,17 +138,20 @@ enhance_kernel(const __grid_constant__ EnhanceArgs a) {
       __syncthreads();   // every thread has read V
 #pragma unroll
       for (int r = 0; r < 4; ++r) {
-        const int i = 4 * ig + r;
 #pragma unroll
         for (int hh = 0; hh < 2; ++hh) {
-          const int off = vofs(i, 8 * vg + 4 * hh);
+          const int off = (i0 + 2 * r + hh) * TV + q0;
           const float4 f = *reinterpret_cast<const float4*>(F + off);
           float2 w01 = make_float2(f.x, f.y), w23 = make_float2(f.z, f.w);
           if (!last) {
             w01 = mul2(w01, w01);
             w23 = mul2(w23, w23);
           }
-          const float2 p01 = mul2(acc[r][2 * hh], w01), p23 = mul2(acc[r][2 * hh + 1], w23);
+          const float2 a01 = hh ? make_float2(acc[r][0].y, acc[r][1].y)
+                                : make_float2(acc[r][0].x, acc[r][1].x);
+          const float2 a23 = hh ? make_float2(acc[r][2].y, acc[r][3].y)
+                                : make_float2(acc[r][2].x, acc[r][3].x);
+          const float2 p01 = mul2(a01, w01), p23 = mul2(a23, w23);
           *reinterpret_cast<float4*>(V + off) = make_float4(p01.x, p01.y, p23.x, p23.y);
         }
       }
@@ -172,13 +165,13 @@ enhance_kernel(const __grid_constant__ EnhanceArgs a) {
         const float tau = fmaf(geo[q], nv[3 * i], fmaf(geo[TV + q], nv[3 * i + 1], geo[2 * TV + q] * nv[3 * i + 2]));
         hv = geo[4 * TV + q] > 0.f ? eval_h<EV>(a.h, tau * geo[3 * TV + q]) : a.h.c0;
       }
-      V[vofs(i, q)] *= hv;
+      V[i * TV + q] *= hv;
     }
     __syncthreads();
     for (int q = t; q < TV; q += NT) {
       if (vox[q] < 0) continue;
       float sum = 0.f;
-      for (int i = 0; i < a.n_o; ++i) sum += V[vofs(i, q)];
+      for (int i = 0; i < a.n_o; ++i) sum += V[i * TV + q];
       const float m = sum * a.n3;
       const float2 fh = a.fh[vox[q]];
       a.A[vox[q]] = make_float2(fh.x * m, fh.y * m);
@@ -364,10 +357,10 @@ int angular_propagator(const double* V, int n, int sh_degree, double tau, std::v
 cudaError_t launch_enhance(const EnhanceArgs& a, int ev, cudaStream_t s) {
   const int n = a.n_o;
   if (n <= 8) return launch_np<8>(a, ev, s);
-  if (n <= 12) return launch_np<12>(a, ev, s);
-  if (n <= 20) return launch_np<20>(a, ev, s);
-  if (n <= 44) return launch_np<44>(a, ev, s);
-  if (n <= kMaxOrientE) return launch_np<kMaxOrientE>(a, ev, s);
+  if (n <= 16) return launch_np<16>(a, ev, s);
+  if (n <= 24) return launch_np<24>(a, ev, s);
+  if (n <= 48) return launch_np<48>(a, ev, s);
+  if (n <= kMaxOrientE) return launch_np<kEStride>(a, ev, s);
   return cudaErrorInvalidValue;
 }
 

@@ -105,7 +105,8 @@ cudaError_t launch_soft_slots(const PassArgs& a, long long nvox, cudaStream_t s)
 
 // Linear left-invariant diffusion (os3d_diffusion.cu): per-frequency
 // integration of the orientation vector; orientation sets up to 68.
-constexpr int kMaxOrientE = 68;
+constexpr int kMaxOrientE = 68;   // largest orientation set of the diffusion kernel
+constexpr int kEStride = 72;      // propagator rows and columns held (a multiple of 8)
 struct EnhanceArgs {
   const float2* fh;           // f_hat G / n^3
   float2* A;                  // out: fh * n^3 h^T E h (then x G/(n^3 max(M,eps)), IDFT);
@@ -121,7 +122,8 @@ struct EnhanceArgs {
   float half_dt;              // t / (2K)
   float D11, D33;
   float nvec[kMaxOrientE][3];
-  float E[kMaxOrientE * kMaxOrientE];   // exp(dt D44 L), row-major, row stride kMaxOrientE
+  float Et[kEStride * kEStride];   // exp(dt D44 L) transposed: Et[j kEStride + i] = E[i][j],
+                                   // zero outside i, j < n_o
   HEval h;
 };
 cudaError_t launch_enhance(const EnhanceArgs& a, int ev, cudaStream_t s);
