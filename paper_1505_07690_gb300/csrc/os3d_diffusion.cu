@@ -25,13 +25,13 @@ namespace {
 
 constexpr double kPiH = 3.141592653589793238462643383279502884;
 
-// One CTA per tile of TV = 128 listed frequencies, NP / 8 warps; NP = the
-// orientation count padded to a multiple of 8. Per Strang step warp w
-// accumulates rows 8w .. 8w+7 of E V, each lane 4 consecutive frequencies:
-// per propagator column j a lane reads its 4 vector entries with one 16-byte
-// shared load and the 8 propagator entries, the same for the whole warp, as
-// four 8-byte shared broadcasts, and issues 16 two-lane FMAs over pairs of
-// adjacent rows. The tile is written back in place after a barrier.
+// One CTA per tile of TV = 128 listed frequencies, NP / R warps; NP = the
+// orientation count padded to a multiple of R rows per warp (R = 6 or 8).
+// Per Strang step warp w accumulates rows R w .. R w + R - 1 of E V, each
+// lane 4 consecutive frequencies: per propagator column j a lane reads its 4
+// vector entries with one 16-byte shared load and the R propagator entries,
+// the same for the whole warp, as R/2 8-byte shared broadcasts, and issues
+// 2R two-lane FMAs over pairs of adjacent rows. The tile is written back in place after a barrier.
 // Vectors are stored [orientation][frequency], rows of TV floats.
 constexpr int kTV = 128;
 
@@ -41,11 +41,12 @@ constexpr size_t enhance_smem() {
          sizeof(int) * 2 * kTV;
 }
 
-template <int NP, int EV>
-__global__ void __launch_bounds__(4 * NP)
+template <int NP, int R, int EV>
+__global__ void __launch_bounds__(32 * NP / R)
 enhance_kernel(const __grid_constant__ EnhanceArgs a) {
-  static_assert(NP % 8 == 0 && NP <= kEStride, "8 propagator rows per warp");
-  constexpr int NT = 4 * NP, TV = kTV;
+  static_assert(R % 2 == 0 && NP % R == 0 && NP % 2 == 0 && NP <= kEStride,
+                "R propagator rows per warp, in pairs; NP^2 floats keep V 16-byte aligned");
+  constexpr int NT = 32 * NP / R, TV = kTV;
   extern __shared__ __align__(16) float esm[];
   float* Es = esm;                       // Es[j * NP + i] = E[i][j]
   float* V = Es + NP * NP;               // [i][q]
@@ -55,8 +56,8 @@ enhance_kernel(const __grid_constant__ EnhanceArgs a) {
   int* vox = reinterpret_cast<int*>(geo + 5 * TV);
   int* mvox = vox + TV;
   const int t = threadIdx.x;
-  const int i0 = 8 * (t >> 5), q0 = 4 * (t & 31);
-  const int nj = (a.n_o + 3) & ~3;       // columns j >= n_o of E are zero
+  const int i0 = R * (t >> 5), q0 = 4 * (t & 31);
+  const int nj = (a.n_o + 1) & ~1;       // columns j >= n_o of E are zero; nj <= NP
 
   for (int q = t; q < NP * NP; q += NT) Es[q] = a.Et[(q / NP) * kEStride + q % NP];
   for (int q = t; q < 3 * NP; q += NT) nv[q] = (q / 3 < a.n_o) ? a.nvec[q / 3][q % 3] : 0.f;
@@ -113,21 +114,21 @@ enhance_kernel(const __grid_constant__ EnhanceArgs a) {
     __syncthreads();
     // ---- K Strang steps: V <- F^2 (E V) (F at the last step)
     for (int s = 0; s < a.steps; ++s) {
-      float2 acc[4][4];   // acc[r][c]: rows i0 + 2r, i0 + 2r + 1 at frequency q0 + c
+      float2 acc[R / 2][4];   // acc[r][c]: rows i0 + 2r, i0 + 2r + 1 at frequency q0 + c
 #pragma unroll
-      for (int r = 0; r < 4; ++r)
+      for (int r = 0; r < R / 2; ++r)
 #pragma unroll
         for (int c = 0; c < 4; ++c) acc[r][c] = make_float2(0.f, 0.f);
 #pragma unroll 1
-      for (int j0 = 0; j0 < nj; j0 += 4) {
+      for (int j0 = 0; j0 < nj; j0 += 2) {
 #pragma unroll
-        for (int jj = 0; jj < 4; ++jj) {
+        for (int jj = 0; jj < 2; ++jj) {
           const int j = j0 + jj;
           const float4 v = *reinterpret_cast<const float4*>(V + j * TV + q0);
           const float2 vv[4] = {make_float2(v.x, v.x), make_float2(v.y, v.y),
                                 make_float2(v.z, v.z), make_float2(v.w, v.w)};
 #pragma unroll
-          for (int r = 0; r < 4; ++r) {
+          for (int r = 0; r < R / 2; ++r) {
             const float2 er = *reinterpret_cast<const float2*>(Es + j * NP + i0 + 2 * r);
 #pragma unroll
             for (int c = 0; c < 4; ++c) acc[r][c] = fma2(er, vv[c], acc[r][c]);
@@ -137,7 +138,7 @@ enhance_kernel(const __grid_constant__ EnhanceArgs a) {
       const bool last = s == a.steps - 1;
       __syncthreads();   // every thread has read V
 #pragma unroll
-      for (int r = 0; r < 4; ++r) {
+      for (int r = 0; r < R / 2; ++r) {
 #pragma unroll
         for (int hh = 0; hh < 2; ++hh) {
           const int off = (i0 + 2 * r + hh) * TV + q0;
@@ -183,21 +184,23 @@ enhance_kernel(const __grid_constant__ EnhanceArgs a) {
   }
 }
 
-template <int NP>
+template <int NP, int R>
 cudaError_t launch_np(const EnhanceArgs& a, int ev, cudaStream_t s) {
+  constexpr int NT = 32 * NP / R;
   int dev = 0, nsm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   constexpr size_t sm = enhance_smem<NP>();
-  auto k = ev == 0 ? enhance_kernel<NP, 0> : (ev == 1 ? enhance_kernel<NP, 1> : enhance_kernel<NP, 2>);
+  auto k = ev == 0 ? enhance_kernel<NP, R, 0>
+                    : (ev == 1 ? enhance_kernel<NP, R, 1> : enhance_kernel<NP, R, 2>);
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   int per_sm = 1;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 4 * NP, sm);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, NT, sm);
   if (e != cudaSuccess) return e;
   const int ntiles = (a.n_in + kTV - 1) / kTV;
   const int grid = std::max(1, std::min(ntiles, nsm * std::max(per_sm, 1)));
-  k<<<grid, 4 * NP, sm, s>>>(a);
+  k<<<grid, NT, sm, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -356,11 +359,13 @@ int angular_propagator(const double* V, int n, int sh_degree, double tau, std::v
 
 cudaError_t launch_enhance(const EnhanceArgs& a, int ev, cudaStream_t s) {
   const int n = a.n_o;
-  if (n <= 8) return launch_np<8>(a, ev, s);
-  if (n <= 16) return launch_np<16>(a, ev, s);
-  if (n <= 24) return launch_np<24>(a, ev, s);
-  if (n <= 48) return launch_np<48>(a, ev, s);
-  if (n <= kMaxOrientE) return launch_np<kEStride>(a, ev, s);
+  // (rows, rows per warp): no padding for the 12- and 42-orientation sets
+  if (n <= 8) return launch_np<8, 8>(a, ev, s);
+  if (n <= 12) return launch_np<12, 6>(a, ev, s);
+  if (n <= 24) return launch_np<24, 8>(a, ev, s);
+  if (n <= 42) return launch_np<42, 6>(a, ev, s);
+  if (n <= 48) return launch_np<48, 8>(a, ev, s);
+  if (n <= kMaxOrientE) return launch_np<kEStride, 8>(a, ev, s);
   return cudaErrorInvalidValue;
 }
 
