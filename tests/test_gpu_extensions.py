@@ -217,8 +217,20 @@ def _diff(M, **kw):
                           sh_degree=d.sh_degree)
 
 
+def _icosa42_plus_two_pairs(seed):
+    """The 42 set and two seeded random directions with their antipodes (46)."""
+    rng = np.random.default_rng(seed)
+    u = rng.standard_normal((2, 3))
+    u /= np.linalg.norm(u, axis=1, keepdims=True)
+    return np.vstack([O.icosa_orientations(1), u, -u])
+
+
+# the orientation counts 6, 12, 18, 42, 46 and 66 reach every row layout of the
+# diffusion kernel (8, 12, 24, 42, 48 and 72 propagator rows)
 @pytest.mark.parametrize("make,sub,dims,kw", [
     (O.icosa_orientations, 1, (32, 32, 32), {}),
+    (O.octa_orientations, 0, (16, 16, 16), dict(t=2.0, steps=2, D44=0.1)),
+    (_icosa42_plus_two_pairs, 5, (16, 16, 16), dict(t=3.0, steps=3, D44=0.05)),
     (O.icosa_orientations, 1, (32, 32, 32), dict(t=2.0, steps=3, D11=0.2, D33=1.0, D44=0.1)),
     (O.octa_orientations, 1, (32, 32, 32), dict(t=4.0, steps=5, D11=0.05, D33=0.5, D44=0.2)),
     (O.icosa_orientations, 0, (16, 16, 16), dict(D44=0.3)),
