@@ -1,0 +1,73 @@
+"""Run-to-run repeatability on the GPU: every kernel of the path is
+deterministic (no atomics, fixed reduction orders), so repeated calls on the
+same input must agree bit for bit. A missing or too weak barrier between the
+CTAs of a plane cluster, or between the two side streams, shows up here as a
+difference between repetitions even where a single call happens to pass the
+parity tolerance."""
+import pytest
+
+from paper_1505_07690_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+REPEATS = 12
+
+
+@pytest.fixture(scope="module")
+def M():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1505_07690_gb300 import build, os3d
+    build.build()
+    return os3d
+
+
+def _same(a, b):
+    import torch
+    if a.is_complex():
+        a, b = torch.view_as_real(a), torch.view_as_real(b)
+    return bool(torch.equal(a, b))
+
+
+def _f(dims, seed):
+    import torch
+    return torch.from_numpy(synth.straight_tubes(dims, 3, seed=seed, noise=0.1))[None].cuda()
+
+
+def test_plane_cluster_path_128(M):
+    """128^3, 42 orientations in blocks of 11 and 10 pairs on two streams:
+    forward, inverse, fused Upsilon and the linear diffusion, repeated."""
+    import torch
+    dims = (128, 128, 128)
+    bank = M.os3d_make_wavelets(dims, M.os3d_icosa_orientations(1), M.os3d_default_params(L=16))
+    f = _f(dims, 71)
+    U0 = M.os3d_forward(bank, f)
+    r0 = M.os3d_inverse(bank, U0)
+    y0 = M.os3d_upsilon(bank, f, 1.5)
+    e0 = M.os3d_enhance_linear(bank, f, M.os3d_default_diffusion())
+    U = torch.empty_like(U0)
+    r, y, e = torch.empty_like(r0), torch.empty_like(y0), torch.empty_like(e0)
+    for _ in range(REPEATS):
+        M.os3d_forward(bank, f, U)
+        M.os3d_inverse(bank, U, r)
+        M.os3d_upsilon(bank, f, 1.5, y)
+        M.os3d_enhance_linear(bank, f, M.os3d_default_diffusion(), e)
+        torch.cuda.synchronize()
+        assert _same(U, U0) and _same(r, r0) and _same(y, y0) and _same(e, e0)
+
+
+def test_plane_cluster_path_256(M):
+    """256^3 planes on 8-CTA clusters, 12 orientations."""
+    import torch
+    dims = (256, 256, 256)
+    bank = M.os3d_make_wavelets(dims, M.os3d_icosa_orientations(0), M.os3d_default_params(L=12))
+    f = _f(dims, 72)
+    U0 = M.os3d_forward(bank, f)
+    r0 = M.os3d_inverse(bank, U0)
+    U, r = torch.empty_like(U0), torch.empty_like(r0)
+    for _ in range(4):
+        M.os3d_forward(bank, f, U)
+        M.os3d_inverse(bank, U, r)
+        torch.cuda.synchronize()
+        assert _same(U, U0) and _same(r, r0)
