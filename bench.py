@@ -191,12 +191,27 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 # roofline bookkeeping
 # ---------------------------------------------------------------------------
+def _code_lines(text):
+    """Source text without // comments, trailing blanks and empty lines (the
+    kernel sources hold no // inside string literals)."""
+    out = []
+    for line in text.splitlines():
+        line = line.split("//", 1)[0].rstrip()
+        if line:
+            out.append(line)
+    return "\n".join(out)
+
+
 def _source_hash():
+    """sha256[:12] of the kernel sources (file names and code, comments
+    excluded): a recorded ncu figure stays valid while this is unchanged."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1505_07690_gb300", "csrc")
     for f in sorted(os.listdir(csrc)):
-        with open(os.path.join(csrc, f), "rb") as fh:
-            h.update(fh.read())
+        if not f.endswith((".cu", ".cuh", ".h")):
+            continue
+        with open(os.path.join(csrc, f), encoding="utf-8") as fh:
+            h.update(f.encode() + b"\0" + _code_lines(fh.read()).encode() + b"\0")
     return h.hexdigest()[:12]
 
 

@@ -10,7 +10,7 @@
 // r_i(w) = D11 (|w|^2 - (w.n_i)^2) + D33 (w.n_i)^2 the symbol of the spatial
 // generators for orientation n_i, and L the discrete Laplace-Beltrami operator
 // on the orientation set (the angular generators A4^2 + A5^2). The score is
-// never formed: one thread integrates the N_o-vector h(w) of its frequency
+// never formed: each CTA integrates the N_o-vectors h(w) of 128 frequencies
 // through the K steps. The angular propagator exp(dt D44 L) is computed on the
 // host in FP64 (closed form through real spherical harmonics) and passed as a
 // kernel parameter.
