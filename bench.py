@@ -134,14 +134,16 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # the oracle on a bounded sample (cpu_baseline and the reference arm)
 # ---------------------------------------------------------------------------
-def oracle_sample_rate(n_orient, repeats=1):
+def oracle_sample_rate(n_orient, repeats=1, workload=None):
     """Oracle forward + exact inverse of the workload volume with a subset of
-    ``n_orient`` of the 162 orientations (a bank of that subset); returns
+    ``n_orient`` of its orientations (a bank of that subset); returns
     (voxel-orientations/s, seconds, description)."""
     import numpy as np
     from oracle import os3d_oracle as O
-    w, synth = _workload_setup()
-    f = synth.workload_volume(WORKLOAD).astype(np.float64)
+    from paper_1505_07690_gb300 import synth
+    workload = workload or WORKLOAD
+    w = synth.WORKLOADS[workload]
+    f = synth.workload_volume(workload).astype(np.float64)
     V = O.icosa_orientations(w["subdiv"])
     half = len(V) // 2
     idx = list(range(n_orient // 2)) + list(range(half, half + n_orient // 2))
@@ -153,7 +155,9 @@ def oracle_sample_rate(n_orient, repeats=1):
         O.inverse(U, bank)
     dt = time.perf_counter() - t0
     nvox = int(np.prod(w["shape"]))
-    return nvox * len(idx) * repeats / dt, dt, f"{len(idx)} of 162 orientations at 128^3, fwd+inv"
+    grid = "x".join(str(n) for n in w["shape"])
+    return (nvox * len(idx) * repeats / dt, dt,
+            f"{len(idx)} of {len(V)} orientations at {grid}, fwd+inv")
 
 
 def run_reference(args):
@@ -737,6 +741,11 @@ def run_precision(args):
             "data": "synthetic", "dtype": "f32",
             "config": {"workload": name, "dims": list(dims), "n_o": len(V), "L": w["L"]},
             "formats": out, "steps": args.steps, "warmup": args.warmup}
+    if not args.no_cpu_baseline:
+        # the FP64 oracle on a bounded sample of the same workload, host cores
+        v, dt, desc = oracle_sample_rate(2, workload=name)
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"{desc} ({dt:.1f} s, numpy FP64, single thread)"}
     print(json.dumps(line), flush=True)
     return 0
 
