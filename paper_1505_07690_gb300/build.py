@@ -81,6 +81,14 @@ def build(verbose: bool = False, jobs: int | None = None) -> str:
         os.replace(LIB + ".tmp", LIB)
         with open(stamp_file, "w") as fh:
             fh.write(stamp)
+    # objects of earlier source states are not needed again
+    keep = {os.path.basename(o) for o in objs}
+    for name in os.listdir(BUILD):
+        if name.endswith(".o") and name not in keep:
+            try:
+                os.remove(os.path.join(BUILD, name))
+            except OSError:
+                pass
     return LIB
 
 
