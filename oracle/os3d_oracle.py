@@ -36,7 +36,11 @@ Legendre values, B-spline convolution, exact recovery of polynomial
 profiles by both fits, great-circle Funk quadrature, the spherical-harmonic
 addition theorem, M ~ 1, Parseval, Hermitian/antipodal symmetry, exact
 reconstruction, grid-symmetry equivariance, the adjoint identity and finite
-differences. Every function below is pinned by at least one of them.
+differences; for the diffusion, harmonic polynomials (the Laplace-Beltrami
+eigenvalues and the angular decay exp(-t D44 l(l+1))), plane waves along and
+across n (D33 and D11 separately), the heat kernel and the splitting order;
+the radial window against the regularised incomplete gamma function and its
+inflection point. Every function below is pinned by at least one of them.
 """
 from __future__ import annotations
 

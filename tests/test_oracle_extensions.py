@@ -6,6 +6,8 @@ other than itself: a spherical design identity, grid rotations, the detector
 semantics the paper states, harmonic polynomials, the heat kernel, the order
 of the splitting and algebraic properties (fixed points, idempotence,
 homogeneity)."""
+import math
+
 import numpy as np
 import pytest
 
@@ -255,3 +257,108 @@ def test_diffused_score_of_a_real_image_keeps_antipodal_conjugacy():
     W = O.diffuse(O.forward(f, bank), bank, O.Diffusion(t=2.0, steps=3, D11=0.2, D33=1.0, D44=0.1))
     h = bank.n_o // 2
     assert np.abs(W[h:] - np.conj(W[:h])).max() < 1e-13 * np.abs(W).max()
+
+
+# ---------------------------------------------------------------------------
+# pins of the individual diffusion rates (Sec. 4.1): the spatial generator
+# D11 (A1^2 + A2^2) + D33 A3^2 acts on a plane wave exp(i w.x) in channel n as
+# multiplication by -[D11 (|w|^2 - (w.n)^2) + D33 (w.n)^2], so a plane wave
+# along n feels only D33 and one across n only D11; the angular generator
+# D44 (A4^2 + A5^2) multiplies a degree-l harmonic of n by -D44 l (l + 1).
+# ---------------------------------------------------------------------------
+def _plane_wave_decay(D11, D33, t=0.7, steps=3):
+    """Per channel, the factor by which ``diffuse`` scales a plane wave along
+    z (D44 = 0, so every Strang step is exact); the wave number and the
+    channel orientations."""
+    dims = (16, 8, 8)
+    bank = O.Bank(dims, O.icosa_orientations(1), O.Params(L=8))
+    kz = 3
+    z = np.arange(dims[0]).reshape(-1, 1, 1)
+    wave = np.broadcast_to(np.exp(2j * np.pi * kz * z / dims[0]), dims)
+    U = np.broadcast_to(wave, (bank.n_o,) + dims).astype(np.complex128)
+    out = O.diffuse(U, bank, O.Diffusion(t=t, steps=steps, D11=D11, D33=D33, D44=0.0))
+    ratio = (out / U).reshape(bank.n_o, -1)
+    assert np.abs(ratio - ratio[:, :1]).max() < 1e-12   # a pure multiplier per channel
+    assert np.abs(ratio.imag).max() < 1e-12
+    return ratio[:, 0].real, 2.0 * np.pi * kz / dims[0], bank.orients
+
+
+def _check_anisotropy(D=0.35, t=0.7):
+    """Diffusion only along n (D33 = D): the channel with n = +-e_z decays by
+    exp(-t D |w|^2) for the wave w along z; the channels with n in the xy-plane
+    (n.w = 0) keep it. Only across n (D11 = D): the reverse."""
+    along, w, V = _plane_wave_decay(0.0, D, t)
+    across, _, _ = _plane_wave_decay(D, 0.0, t)
+    par = np.abs(np.abs(V[:, 2]) - 1.0) < 1e-12
+    perp = np.abs(V[:, 2]) < 1e-12
+    assert par.sum() == 2 and perp.sum() >= 4
+    full = math.exp(-t * D * w * w)
+    err = max(np.abs(along[par] - full).max(), np.abs(along[perp] - 1.0).max(),
+              np.abs(across[par] - 1.0).max(), np.abs(across[perp] - full).max())
+    return err
+
+
+def test_spatial_diffusion_along_and_across_the_orientation():
+    assert _check_anisotropy() < 1e-12
+
+
+def _check_angular_rate(D44=0.3, t=1.1, steps=5):
+    """U_i(x) = Y(n_i) g(x) with Y a harmonic polynomial of degree l <= the
+    operator's degree decays as exp(-t D44 l (l + 1)) for any number of Strang
+    steps (D11 = D33 = 0)."""
+    dims = (6, 6, 6)
+    bank = O.Bank(dims, O.icosa_orientations(1), O.Params(L=8))
+    g = np.random.default_rng(40).standard_normal(dims)
+    x, y, z = bank.orients.T
+    err = 0.0
+    for Y, l in ((z, 1), (x * y, 2), (x * x - y * y, 2), (x * y * z, 3), (x ** 3 - 3 * x * y * y, 3)):
+        U = Y[:, None, None, None] * g[None]
+        out = O.diffuse(U.astype(np.complex128), bank,
+                        O.Diffusion(t=t, steps=steps, D11=0.0, D33=0.0, D44=D44))
+        err = max(err, np.abs(out - math.exp(-t * D44 * l * (l + 1)) * U).max() / np.abs(U).max())
+    return err
+
+
+def test_angular_diffusion_rate_of_harmonics():
+    assert _check_angular_rate() < 1e-12
+
+
+def test_rate_pins_fail_on_planted_mistakes(monkeypatch):
+    """The two pins above reject the mistakes a shared reading could make: the
+    rates D11 and D33 swapped, and a wrong step factor on dt D44."""
+    real_rates = O.spatial_rates
+
+    def swapped(bank, D):
+        return real_rates(bank, O.Diffusion(t=D.t, steps=D.steps, D11=D.D33, D33=D.D11,
+                                            D44=D.D44, sh_degree=D.sh_degree))
+
+    with monkeypatch.context() as m:
+        m.setattr(O, "spatial_rates", swapped)
+        assert _check_anisotropy() > 1e-2
+    real_expm = O.scipy.linalg.expm
+    with monkeypatch.context() as m:
+        m.setattr(O.scipy.linalg, "expm", lambda A: real_expm(0.5 * A))   # dt/2 instead of dt
+        assert _check_angular_rate() > 1e-2
+    with monkeypatch.context() as m:
+        m.setattr(O.scipy.linalg, "expm", lambda A: real_expm(2.0 * A))
+        assert _check_angular_rate() > 1e-2
+
+
+# ---------------------------------------------------------------------------
+# radial window g = M_N(rho^2 / t) (Sec. 3.1)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("N,gamma", [(8, 0.8), (20, 0.8), (20, 0.85), (3, 0.5)])
+def test_radial_window_is_the_regularised_upper_gamma_with_its_inflection_at_gamma_rho_n(N, gamma):
+    """exp(-x) sum_{k<=N} x^k / k! is the regularised upper incomplete gamma
+    function Q(N + 1, x) (a library routine); as a function of rho its second
+    derivative changes sign at gamma rho_N, the inflection point Sec. 3.1
+    places there by the choice of t."""
+    import scipy.special
+    rho = np.linspace(0.0, 1.8 * np.pi, 301)
+    t = O.radial_t(N, gamma)
+    assert np.abs(O.radial_window(rho, N, gamma) - scipy.special.gammaincc(N + 1, rho ** 2 / t)).max() < 1e-13
+    r0, h = gamma * np.pi, 1e-3
+    d2 = lambda r: (O.radial_window(r + h, N, gamma) - 2 * O.radial_window(r, N, gamma)
+                    + O.radial_window(r - h, N, gamma)) / h ** 2
+    assert d2(r0 - 0.02) < 0.0 < d2(r0 + 0.02)
+    assert abs(d2(r0)) < 1e-3 * abs(d2(r0 - 0.3))
