@@ -29,7 +29,8 @@ import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
-# the oracle legs are reported as single-core: keep numpy's BLAS to one thread
+# the oracle runs as one single-threaded process per host core: keep numpy's
+# BLAS to one thread in each (the spawned workers inherit this)
 for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
     os.environ.setdefault(_v, "1")
 
@@ -132,59 +133,154 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------
-# the oracle on a bounded sample (cpu_baseline and the reference arm)
+# the oracle on all host cores (cpu_baseline and the reference arm)
 # ---------------------------------------------------------------------------
-def oracle_sample_rate(n_orient, repeats=1, workload=None):
-    """Oracle forward + exact inverse of the workload volume with a subset of
-    ``n_orient`` of its orientations (a bank of that subset); returns
-    (voxel-orientations/s, seconds, description)."""
+_OW = {}
+
+
+def _ow_init(dims, orients, L, shm_in, shm_out, slots):
+    import numpy as np
+    from multiprocessing import shared_memory
+    from oracle import os3d_oracle as O
+    _OW["O"] = O
+    _OW["bank"] = O.Bank(dims, orients, O.Params(L=L))
+    _OW["shm"] = (shared_memory.SharedMemory(name=shm_in), shared_memory.SharedMemory(name=shm_out))
+    _OW["f"] = np.ndarray(dims, np.float64, buffer=_OW["shm"][0].buf)
+    _OW["out"] = np.ndarray((slots,) + tuple(dims), np.complex128, buffer=_OW["shm"][1].buf)
+
+
+def _ow_m_part(job):
+    slot, idx = job
+    _OW["out"][slot] = _OW["bank"].M_part(idx)
+    return slot
+
+
+def _ow_transform_part(job):
+    """The oracle's forward transform of the shared volume for the
+    orientations idx, then their part of the inverse's orientation sum."""
+    slot, idx = job
+    O, bank = _OW["O"], _OW["bank"]
+    U = O.forward(_OW["f"], bank, idx)
+    _OW["out"][slot] = O.backproject(U, bank, idx)
+    return slot
+
+
+class OracleOnCores:
+    """The FP64 oracle's forward transform and exact inverse of one volume,
+    its orientations dealt over one single-threaded process per host core
+    (spawned, so that no process is forked after the first GPU call). The
+    orientation sums of the inverse and of M are added up from the parts and
+    the last step of the inverse runs here: the result is the oracle's
+    inverse(forward(f)) up to the order of the orientation sum."""
+
+    def __init__(self, dims, orients, L, f, cores=None):
+        import multiprocessing as mp
+        import numpy as np
+        from multiprocessing import shared_memory
+        from oracle import os3d_oracle as O
+        self.O = O
+        self.dims = tuple(int(d) for d in dims)
+        orients = np.asarray(orients, dtype=np.float64)
+        n_o = len(orients)
+        self.cores = max(1, min(cores or os.cpu_count() or 1, n_o))
+        self.parts = [list(range(k, n_o, self.cores)) for k in range(self.cores)]
+        nvox = int(np.prod(self.dims))
+        self.shm_in = shared_memory.SharedMemory(create=True, size=nvox * 8)
+        self.shm_out = shared_memory.SharedMemory(create=True, size=self.cores * nvox * 16)
+        self.f = np.ndarray(self.dims, np.float64, buffer=self.shm_in.buf)
+        self.f[...] = f
+        self.out = np.ndarray((self.cores,) + self.dims, np.complex128, buffer=self.shm_out.buf)
+        self.bank = O.Bank(self.dims, orients, O.Params(L=L))
+        self.pool = mp.get_context("spawn").Pool(
+            self.cores, initializer=_ow_init,
+            initargs=(self.dims, orients, L, self.shm_in.name, self.shm_out.name, self.cores))
+        # bank construction (untimed, as on the GPU): M from its parts
+        self.pool.map(_ow_m_part, list(enumerate(self.parts)), chunksize=1)
+        self.bank.set_M(self.out.real.sum(axis=0))
+
+    def step(self):
+        """One forward + exact inverse; (f_rec, seconds)."""
+        t0 = time.perf_counter()
+        self.pool.map(_ow_transform_part, list(enumerate(self.parts)), chunksize=1)
+        f_rec = self.O.reconstruct(self.out.sum(axis=0), self.bank)
+        return f_rec, time.perf_counter() - t0
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+        del self.f, self.out
+        for m in (self.shm_in, self.shm_out):
+            m.close()
+            m.unlink()
+
+
+def oracle_on_cores(workload, steps=1, cores=None):
+    """(voxel-orientations/s, f_rec, description) of the oracle on the whole
+    named workload (all its orientations, forward + inverse) on the host cores."""
     import numpy as np
     from oracle import os3d_oracle as O
     from paper_1505_07690_gb300 import synth
-    workload = workload or WORKLOAD
     w = synth.WORKLOADS[workload]
     f = synth.workload_volume(workload).astype(np.float64)
     V = O.icosa_orientations(w["subdiv"])
-    half = len(V) // 2
-    idx = list(range(n_orient // 2)) + list(range(half, half + n_orient // 2))
-    bank = O.Bank(w["shape"], V[idx], O.Params(L=w["L"]))
-    bank.M()   # bank construction is outside the timed region, as on the GPU
-    t0 = time.perf_counter()
-    for _ in range(repeats):
-        U = O.forward(f, bank)
-        O.inverse(U, bank)
-    dt = time.perf_counter() - t0
+    oc = OracleOnCores(w["shape"], V, w["L"], f, cores)
+    try:
+        dt = 0.0
+        for _ in range(steps):
+            f_rec, t = oc.step()
+            dt += t
+    finally:
+        oc.close()
     nvox = int(np.prod(w["shape"]))
     grid = "x".join(str(n) for n in w["shape"])
-    return (nvox * len(idx) * repeats / dt, dt,
-            f"{len(idx)} of {len(V)} orientations at {grid}, fwd+inv")
+    desc = (f"the whole {grid} x {len(V)} workload ({workload}), forward + exact inverse, "
+            f"{steps} step(s) in {dt:.1f} s; orientations split over {oc.cores} single-threaded "
+            f"numpy FP64 processes")
+    return nvox * len(V) * steps / dt, f_rec, desc, oc.cores
+
+
+def _config(dims, n_o, L, udtype="c64", world=1):
+    nvox = int(dims[0] * dims[1] * dims[2])
+    esize = 4 if udtype == "bf16x2" else 8
+    return {"workload": WORKLOAD, "dims": list(dims), "n_o": n_o, "L": L, "batch_per_gpu": 1,
+            "udtype": udtype, "parallelism": f"replicas{world}",
+            "l2": f"inputs larger than L2 (U = {n_o * nvox * esize / 1e9:.2f} GB)"}
 
 
 def run_reference(args):
+    """The oracle as the reference arm: every step is the whole workload
+    (forward + exact inverse of one volume with all its orientations) on all
+    host cores; rank 0 only."""
     world, rank, _ = _dist()
     if rank != 0:
         return 0
-    per_step = 2
-    for _ in range(args.warmup):
-        oracle_sample_rate(per_step)
-    times = []
-    vals = []
-    for _ in range(args.steps):
-        v, dt, desc = oracle_sample_rate(per_step)
-        times.append(dt)
-        vals.append(v)
-    tot = sum(times)
     import numpy as np
-    nvox = 128 ** 3
-    value = nvox * per_step * args.steps / tot
+    from oracle import os3d_oracle as O
+    from paper_1505_07690_gb300 import synth
+    w = synth.WORKLOADS[WORKLOAD]
+    f = synth.workload_volume(WORKLOAD).astype(np.float64)
+    V = O.icosa_orientations(w["subdiv"])
+    oc = OracleOnCores(w["shape"], V, w["L"], f)
+    try:
+        for _ in range(args.warmup):
+            oc.step()
+        times = [oc.step()[1] for _ in range(args.steps)]
+    finally:
+        oc.close()
+    tot = sum(times)
+    nvox = int(np.prod(w["shape"]))
+    value = nvox * len(V) * args.steps / tot
+    desc = (f"every step the whole workload: forward + exact inverse of one volume with all "
+            f"{len(V)} orientations, split over {oc.cores} single-threaded numpy FP64 processes")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "dims": [128, 128, 128], "n_o": 162, "L": 16,
-                   "step_sample": f"{per_step} of 162 orientations, fwd+inv"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+        "config": _config(w["shape"], len(V), w["L"], world=world),
+        "latency_ms": {"p50": 1e3 * float(np.percentile(times, 50)),
+                       "p99": 1e3 * float(np.percentile(times, 99))},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": oc.cores, "kind": "oracle",
                          "sample": desc},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -570,11 +666,35 @@ def run_ours(args):
         "fp32_peak_tflops": fp32_peak,
         "frac_fp32": flops / (k_ms / 1e3) / 1e12 / fp32_peak}
 
+    # BF16 storage of the score on the same workload (precision form)
+    Ub = os3d.new_score(bank, 1, bf16=True)
+    fb = torch.empty_like(f)
+
+    def step_bf16():
+        os3d.os3d_forward(bank, f, Ub)
+        os3d.os3d_inverse(bank, Ub, fb)
+
+    ms_b = timed(step_bf16, args.steps)
+    ops["bf16_headline"] = {
+        "ms": ms_b, "value": nvox * n_o / (ms_b / 1e3), "unit": UNIT, "udtype": "bf16x2",
+        "score_gb": Ub.numel() * Ub.element_size() / 1e9,
+        "recon_rel_l2_vs_c64": float(torch.linalg.vector_norm(fb - frec) /
+                                     torch.linalg.vector_norm(frec))}
+    del Ub, fb
+    torch.cuda.empty_cache()
+    if world == 1:
+        # precision form at 256^3 x 42 and serving, short bounded legs
+        ops["precision"] = precision_leg(3, 3)
+        ops["serving"] = serve_mix(300, 0.8, False)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, dt, desc = oracle_sample_rate(8)
-        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"{desc} ({dt:.1f} s, numpy FP64, single thread)"}
+        v, fo, desc, cores = oracle_on_cores(WORKLOAD)
+        fg = frec[0].cpu().numpy().astype(np.float64)
+        v1, _, desc1, cores1 = oracle_on_cores("tubes32_no42")
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc,
+               "gpu_recon_rel_l2_vs_oracle": float(np.linalg.norm(fg - fo) / np.linalg.norm(fo)),
+               "tubes32_no42": {"value": v1, "unit": UNIT, "cores": cores1, "sample": desc1}}
 
     if rank == 0:
         lat = sorted(step_ms)
@@ -582,10 +702,7 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "dims": list(dims), "n_o": n_o, "L": w["L"],
-                       "batch_per_gpu": 1, "udtype": "bf16x2" if args.bf16 else "c64",
-                       "parallelism": f"replicas{world}",
-                       "l2": f"inputs larger than L2 (U = {n_o * nvox * esize / 1e9:.2f} GB)"},
+            "config": _config(dims, n_o, w["L"], "bf16x2" if args.bf16 else "c64", world),
             "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
             "roofline": roof,
             "step_hbm": {"bytes": step_bytes, "achieved_gbs": step_bytes / (total_ms / args.steps / 1e3) / 1e9},
@@ -611,22 +728,32 @@ SERVE_SUBDIVS = [1, 2]   # 42 or 162 orientations
 
 
 def run_serve(args):
-    import numpy as np
     import torch
-    from paper_1505_07690_gb300 import build, os3d, synth
+    from paper_1505_07690_gb300 import build
     world, rank, local = _dist()
     torch.cuda.set_device(local)
     build.build()
-    rng = np.random.default_rng(rank)
+    print(json.dumps(serve_mix(args.serve, args.load, args.bf16, seed=rank)), flush=True)
+    return 0
+
+
+def serve_mix(n_requests, load, bf16, seed=0):
+    """``n_requests`` requests of the mixed workload through the server: first
+    all queued at once (capacity), then Poisson arrivals at ``load`` x that
+    capacity; p50/p99 latency of the second run."""
+    import numpy as np
+    import torch
+    from paper_1505_07690_gb300 import os3d, synth
+    rng = np.random.default_rng(seed)
     # volume pool: 2 seeded spline-tube volumes per shape (volume seed 1000 + k)
     pool = {sh: [torch.from_numpy(synth.spline_tubes(sh, 6, seed=1000 + k, noise=0.2)).pin_memory()
                  for k in range(2)] for sh in SERVE_SHAPES}
     reqs = [(SERVE_SHAPES[rng.integers(len(SERVE_SHAPES))], SERVE_SUBDIVS[rng.integers(2)],
-             int(rng.integers(2))) for _ in range(args.serve)]
+             int(rng.integers(2))) for _ in range(n_requests)]
     n_o = {1: 42, 2: 162}
     vo = [int(np.prod(sh)) * n_o[sd] for sh, sd, _ in reqs]
     srv = os3d.Server(os3d.os3d_server_default_config(arena_bytes=24 << 30, max_inflight=4,
-                                                      udtype=1 if args.bf16 else 0),
+                                                      udtype=1 if bf16 else 0),
                       os3d.os3d_default_params(L=16))
 
     def drain(outstanding, lat, block):
@@ -654,7 +781,8 @@ def run_serve(args):
     t_cap = time.perf_counter() - t0
     capacity = len(reqs) / t_cap
     # Poisson arrivals at load x capacity
-    rate = args.load * capacity
+    done0, cap0, rep0 = srv.stats()
+    rate = load * capacity
     gaps = rng.exponential(1.0 / rate, len(reqs))
     out, lat = [], []
     t0 = time.perf_counter()
@@ -669,35 +797,49 @@ def run_serve(args):
     t_run = time.perf_counter() - t0
     done, captured, replayed = srv.stats()
     srv.close()
+    torch.cuda.empty_cache()
     line = {
         "metric": "serving: forward+inverse per request, mixed sizes, Poisson arrivals; p50/p99 latency",
         "value": sum(vo) / t_run, "unit": UNIT, "n_gpus": 1, "higher_is_better": True,
         "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                        "mean": float(np.mean(lat))},
         "requests": len(reqs), "requests_per_s": len(reqs) / t_run,
-        "capacity_requests_per_s": capacity, "load": args.load,
-        "graphs": {"captured": captured, "replays": replayed, "completed": done},
+        "capacity_requests_per_s": capacity, "load": load,
+        "graphs": {"captured": captured, "replays": replayed, "completed": done,
+                   "poisson_run": {"requests": done - done0, "captured": captured - cap0,
+                                   "replays": replayed - rep0,
+                                   "replay_fraction": (replayed - rep0) / max(done - done0, 1)}},
         "dtype": "f32", "data": "synthetic",
         "config": {"workload": "serve_mix", "shapes": SERVE_SHAPES, "n_o": [42, 162], "L": 16,
-                   "arrival": "poisson", "udtype": "bf16x2" if args.bf16 else "c64",
+                   "arrival": "poisson", "udtype": "bf16x2" if bf16 else "c64",
                    "max_inflight": 4, "arena_gb": 24},
     }
-    print(json.dumps(line), flush=True)
-    return 0
+    return line
 
 
 # ---------------------------------------------------------------------------
 # precision form: complex64 and BF16 storage of U against the exact result
 # ---------------------------------------------------------------------------
 def run_precision(args):
+    from paper_1505_07690_gb300 import build
+    build.build()
+    line = precision_leg(args.steps, args.warmup)
+    if not args.no_cpu_baseline:
+        v, _, desc, cores = oracle_on_cores("splines256_no42")
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                "sample": desc}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def precision_leg(steps, warmup):
     """256^3, 40 spline tubes, 42 orientations, L = 20. For each storage
     format: the relative L2 error of W^-1 W f against the exactly known
     IDFT[1_ball f_hat] (numpy FP64), and of the BF16 score against the
     complex64 one; plus the forward+inverse time of each format."""
     import numpy as np
     import torch
-    from paper_1505_07690_gb300 import build, os3d, synth
-    build.build()
+    from paper_1505_07690_gb300 import os3d, synth
     name = "splines256_no42"
     w = synth.WORKLOADS[name]
     dims = w["shape"]
@@ -714,19 +856,19 @@ def run_precision(args):
     for fmt in ("c64", "bf16"):
         U = os3d.new_score(bank, 1, bf16=(fmt == "bf16"))
         fr = torch.empty_like(f)
-        for _ in range(max(args.warmup, 3)):
+        for _ in range(max(warmup, 3)):
             os3d.os3d_forward(bank, f, U)
             os3d.os3d_inverse(bank, U, fr)
         torch.cuda.synchronize()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record()
-        for _ in range(args.steps):
+        for _ in range(steps):
             os3d.os3d_forward(bank, f, U)
             os3d.os3d_inverse(bank, U, fr)
         b.record()
         torch.cuda.synchronize()
         err = float(np.linalg.norm(fr.cpu().numpy() - fb) / np.linalg.norm(fb))
-        rec = {"recon_rel_l2_vs_exact": err, "ms_per_fwd_inv": a.elapsed_time(b) / args.steps,
+        rec = {"recon_rel_l2_vs_exact": err, "ms_per_fwd_inv": a.elapsed_time(b) / steps,
                "score_gb": U.numel() * U.element_size() / 1e9}
         if fmt == "c64":
             Uc = U[0, :4].clone()
@@ -740,14 +882,10 @@ def run_precision(args):
     line = {"metric": "precision form: relative L2 error of the reconstruction per score format",
             "data": "synthetic", "dtype": "f32",
             "config": {"workload": name, "dims": list(dims), "n_o": len(V), "L": w["L"]},
-            "formats": out, "steps": args.steps, "warmup": args.warmup}
-    if not args.no_cpu_baseline:
-        # the FP64 oracle on a bounded sample of the same workload, host cores
-        v, dt, desc = oracle_sample_rate(2, workload=name)
-        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                "sample": f"{desc} ({dt:.1f} s, numpy FP64, single thread)"}
-    print(json.dumps(line), flush=True)
-    return 0
+            "formats": out, "steps": steps, "warmup": warmup}
+    del f, bank
+    torch.cuda.empty_cache()
+    return line
 
 
 def main():

@@ -29,7 +29,11 @@
  * (4 bytes). Re U = line response, Im U = edge response (Sec. 3, requirement 6).
  *
  * Ownership: the caller owns every data buffer (device pointers). A bank owns
- * its coefficients, M^-1 and one default workspace until os3d_destroy_bank.
+ * its coefficients and per-voxel factors until os3d_destroy_bank, and also a
+ * default workspace, which the first transform call made with a NULL
+ * workspace allocates (cudaMalloc, so that call must not be under stream
+ * capture; ENOMEM if it fails). Callers that always pass a workspace never
+ * cause that allocation.
  * Ordering: every call that takes a stream only enqueues work on it and
  * returns; none synchronises the device, except os3d_make_wavelets, which
  * synchronises its own stream once (it copies the fitted coefficients back).
@@ -231,10 +235,17 @@ os3d_status os3d_angular_propagator(const double* orient, int n, int sh_degree, 
 os3d_status os3d_enhance_linear(const os3d_bank* bank, const float* f, int batch, float* f_out,
                                 const os3d_diffusion* d, void* workspace, void* stream);
 
-/* Sizes: workspace bytes one call needs, and device bytes of one volume's
- * score (N_o x nz x ny x nx x 8). Host only. */
+/* Sizes: workspace bytes one call needs, and the device bytes one volume
+ * occupies through forward + inverse: its complex64 score (N_o x nz x ny x nx
+ * x 8) plus the input and the output image (2 x nz x ny x nx x 4); a BF16X2
+ * score takes half of the score's part. Either pointer may be NULL. Host only. */
 os3d_status os3d_bank_info(const os3d_bank* bank, size_t* workspace_bytes,
-                           size_t* score_bytes_per_volume);
+                           size_t* footprint_bytes_per_volume);
+
+/* Device bytes the bank itself holds now: its three per-voxel float tables,
+ * the in-ball frequency list and, once allocated, its default workspace.
+ * Host only. Errors: EINVAL (NULL). */
+os3d_status os3d_bank_resident_bytes(const os3d_bank* bank, size_t* bytes);
 
 /* Copies of bank data for inspection: the Legendre coefficients b (of A) and
  * c (of h = h_Re + h_Im, normalised), L + 1 doubles each (host); and, on the
@@ -255,8 +266,13 @@ const char* os3d_status_string(os3d_status s);
  * admitted in arrival order as soon as one of max_inflight stream slots and
  * the request's footprint (score + two images + workspace) in the arena are
  * free; admitted requests run concurrently. Wavelet banks are made on first
- * use per (grid, orientation set) with the server's parameters and kept until
- * os3d_server_destroy. f and f_out must stay valid until the request is
+ * use per (grid, orientation set) with the server's parameters and cached;
+ * when the banks' resident bytes (os3d_bank_resident_bytes) would exceed
+ * bank_cache_bytes, idle banks (no request in flight) are destroyed, least
+ * recently used first. Placement: each bank remembers up to 2 x max_inflight
+ * arena offsets ("homes") where its requests ran; a request takes the first
+ * free home of its bank, else the first free range that fits (recorded as a
+ * new home while there is room). f and f_out must stay valid until the request is
  * complete and should be page-locked (pageable host memory makes the copies,
  * and with them the worker thread, synchronous). The server must be created,
  * used and destroyed with one device current. */
@@ -264,17 +280,18 @@ typedef struct {
   size_t arena_bytes;  /* device memory for in-flight requests                  */
   int max_inflight;    /* concurrent requests (streams), 1..64                  */
   int udtype;          /* score storage of every request: OS3D_U_C64 or BF16X2  */
-  int use_graphs;      /* 1: the kernels of forward + inverse for one (bank, arena
-                          offset) are captured as a CUDA graph when that pair occurs
-                          for the second time and replayed by every later request
-                          on it (up to 512 graphs, then the cache is cleared); a
-                          pair seen once runs with direct launches. 0: direct
-                          launches only                                            */
+  int use_graphs;      /* 1: the kernels of forward + inverse for one (bank, home)
+                          are captured as a CUDA graph on the first request placed
+                          there and replayed by every later one (up to 512 graphs,
+                          then the cache is cleared; a bank's graphs go with it);
+                          requests placed outside their bank's homes run with
+                          direct launches. 0: direct launches only                */
+  size_t bank_cache_bytes; /* budget for the resident bytes of cached banks, > 0   */
 } os3d_server_config;
 typedef struct os3d_server os3d_server;
 
-/* arena_bytes = 16 GiB, max_inflight = 4, udtype = OS3D_U_C64, use_graphs = 1.
- * Host only. */
+/* arena_bytes = 16 GiB, max_inflight = 4, udtype = OS3D_U_C64, use_graphs = 1,
+ * bank_cache_bytes = 4 GiB. Host only. */
 os3d_status os3d_server_default_config(os3d_server_config* cfg);
 /* Errors: EINVAL (config out of range), ENOMEM (arena), ECUDA. p may be NULL
  * (defaults). */
@@ -310,9 +327,11 @@ os3d_status os3d_server_destroy(os3d_server* s);
  * Limits: volumes of at most OS3D_STATIC_MAX_VOXELS voxels (64^3); larger
  * banks are rejected with OS3D_EINVAL. The array (3 x OS3D_STATIC_MAX_VOXELS
  * complex floats, 6 MiB) is held by every GPU that loads the library until
- * the process exits. The first call on each device looks up the array's
- * device address (cudaGetSymbolAddress) with that device current; make that
- * first call before any stream capture. All calls share the one array and it
+ * the process exits. The first call in each CUDA context of a device looks
+ * up the array's device address (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture. A context created
+ * anew (for instance after cudaDeviceReset) is recognised by its unique id and
+ * gets a fresh lookup on its first call. All calls share the one array and it
  * keeps the last call's contents (every element is overwritten before it is
  * read, so nothing needs clearing); calls that overlap on the GPU (other
  * streams, other threads) race on it and must be serialised by the caller.

@@ -394,14 +394,26 @@ class Bank:
         """Real Fourier multiplier psi_hat_i on the DFT grid (nz, ny, nx)."""
         return self.G * self.angular(i)
 
+    def M_part(self, orients_idx):
+        """sum over the given orientations of |psi_hat_i|^2 (M splits into such
+        parts over a partition of the orientations)."""
+        M = np.zeros(self.dims)
+        for i in orients_idx:
+            M += self.psi_hat(i) ** 2
+        return M
+
     def M(self):
         """M_psi^d = sum_i |psi_hat_i|^2 (Sec. 2.1; constants absorbed in kappa)."""
         if self._M is None:
-            M = np.zeros(self.dims)
-            for i in range(self.n_o):
-                M += self.psi_hat(i) ** 2
-            self._M = M
+            self._M = self.M_part(range(self.n_o))
         return self._M
+
+    def set_M(self, M):
+        """Installs M summed from M_part over a partition of the orientations
+        (computed elsewhere, e.g. in parallel)."""
+        M = np.asarray(M, dtype=np.float64)
+        assert M.shape == self.dims
+        self._M = M
 
     def M_inv(self):
         """1 / max(M, eps) where M > 0, else 0 (Sec. 3.1 clamp)."""
@@ -424,20 +436,29 @@ def forward(f, bank: Bank, orients_idx=None):
     return np.stack([forward_one(fhat, bank, i) for i in idx])
 
 
-def backproject(U, bank: Bank):
-    """sum_i psi_hat_i * DFT(U_i): the DFT of sum_i (psi_check_i * U_i)."""
+def backproject(U, bank: Bank, orients_idx=None):
+    """sum_i psi_hat_i * DFT(U_i): the DFT of sum_i (psi_check_i * U_i); with
+    ``orients_idx`` the sum over those orientations only, U[j] holding
+    orientation orients_idx[j] (the orientation sum splits into such parts)."""
+    idx = range(bank.n_o) if orients_idx is None else orients_idx
     acc = np.zeros(bank.dims, dtype=np.complex128)
-    for i in range(bank.n_o):
-        acc += bank.psi_hat(i) * np.fft.fftn(U[i])
+    for j, i in enumerate(idx):
+        acc += bank.psi_hat(i) * np.fft.fftn(U[j])
     return acc
+
+
+def reconstruct(acc, bank: Bank, real=True):
+    """IDFT[ max(M, eps)^-1 acc ] of an orientation sum acc = sum_i psi_hat_i
+    DFT(U_i) (the last step of Eq. Reconstruction1Discrete)."""
+    f = np.fft.ifftn(acc * bank.M_inv())
+    return f.real if real else f
 
 
 def inverse(U, bank: Bank, real=True):
     """Exact reconstruction f = IDFT[ max(M, eps)^-1 sum_i psi_hat_i DFT(U_i) ]
     (Eq. Reconstruction1Discrete with the Sec. 3.1 clamp); the real part is
     the reconstructed real image."""
-    f = np.fft.ifftn(backproject(U, bank) * bank.M_inv())
-    return f.real if real else f
+    return reconstruct(backproject(U, bank), bank, real)
 
 
 def adjoint(G, bank: Bank, real=True):

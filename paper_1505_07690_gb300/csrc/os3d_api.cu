@@ -106,7 +106,9 @@ struct os3d_bank {
   int4* seg = nullptr;                 // frequencies inside the ball, as row segments
   int nseg = 0, n_in = 0;              // (half of them when every orientation is paired)
   int mirror = 0;
-  void* ws = nullptr;                  // default workspace
+  mutable void* ws = nullptr;          // default workspace, allocated by the first call
+                                       // that passes no workspace of its own
+  mutable std::mutex ws_mu;
   cudaStream_t side[2] = {nullptr, nullptr};   // consecutive blocks alternate between these
   cudaEvent_t ev_fork = nullptr, ev_join[2] = {nullptr, nullptr};
   size_t ws_bytes = 0;
@@ -536,8 +538,7 @@ os3d_status os3d_make_wavelets(const int dims[3], const double* orient, int n_o,
   // device allocations
   if (cudaMalloc(&b->Gs, sizeof(float) * b->nvox) != cudaSuccess ||
       cudaMalloc(&b->GM, sizeof(float) * b->nvox) != cudaSuccess ||
-      cudaMalloc(&b->Minv, sizeof(float) * b->nvox) != cudaSuccess ||
-      cudaMalloc(&b->ws, b->ws_bytes) != cudaSuccess) {
+      cudaMalloc(&b->Minv, sizeof(float) * b->nvox) != cudaSuccess) {
     cudaGetLastError();
     return fail(OS3D_ENOMEM);
   }
@@ -660,10 +661,19 @@ os3d_status os3d_make_wavelets(const int dims[3], const double* orient, int n_o,
   return OS3D_OK;
 }
 
-os3d_status os3d_bank_info(const os3d_bank* b, size_t* ws, size_t* score_bytes) {
+os3d_status os3d_bank_info(const os3d_bank* b, size_t* ws, size_t* footprint) {
   if (!b) return OS3D_EINVAL;
   if (ws) *ws = b->ws_bytes;
-  if (score_bytes) *score_bytes = sizeof(float2) * (size_t)b->nvox * b->n_o;
+  // one volume through forward + inverse: its complex64 score and two images
+  if (footprint) *footprint = sizeof(float2) * (size_t)b->nvox * b->n_o + 2 * sizeof(float) * (size_t)b->nvox;
+  return OS3D_OK;
+}
+
+os3d_status os3d_bank_resident_bytes(const os3d_bank* b, size_t* bytes) {
+  if (!b || !bytes) return OS3D_EINVAL;
+  std::lock_guard<std::mutex> lk(b->ws_mu);
+  *bytes = 3 * sizeof(float) * (size_t)b->nvox + sizeof(int4) * (size_t)b->nseg +
+           (b->ws ? b->ws_bytes : 0);
   return OS3D_OK;
 }
 
@@ -714,8 +724,8 @@ struct Work {
   float2* T[2];   // block intermediates (one set per side stream)
 };
 
-Work carve(const os3d_bank* b, void* ws) {
-  float2* base = (float2*)(ws ? ws : b->ws);
+Work carve_base(const os3d_bank* b, void* base_ptr) {
+  float2* base = (float2*)base_ptr;
   const long long n = b->nvox;
   Work w;
   w.fh = base;
@@ -725,6 +735,24 @@ Work carve(const os3d_bank* b, void* ws) {
   w.T[0] = base + 4 * n;
   w.T[1] = base + (4 + b->block_slots) * n;
   return w;
+}
+
+// The caller's workspace, or the bank's own, which the first call that needs
+// it allocates (cudaMalloc; outside stream capture).
+os3d_status workspace_for(const os3d_bank* b, void* ws, Work* out) {
+  if (!ws) {
+    std::lock_guard<std::mutex> lk(b->ws_mu);
+    if (!b->ws) {
+      if (fault_is("alloc_ws") || cudaMalloc(&b->ws, b->ws_bytes) != cudaSuccess) {
+        cudaGetLastError();
+        b->ws = nullptr;
+        return OS3D_ENOMEM;
+      }
+    }
+    ws = b->ws;
+  }
+  *out = carve_base(b, ws);
+  return OS3D_OK;
 }
 
 // fork the two side streams off `s` / join them back into `s`
@@ -898,7 +926,8 @@ os3d_status finish_real(const os3d_bank* b, const Work& w, int nblocks, const fl
 // z-pass.
 os3d_status backward_impl(const os3d_bank* b, const void* U, int udtype, int batch, float* fout,
                           void* ws, cudaStream_t s, bool use_m) {
-  const Work w = carve(b, ws);
+  Work w;
+  if (const os3d_status e = workspace_for(b, ws, &w)) return e;
   const int nz = b->dims[0], ny = b->dims[1], nx = b->dims[2];
   const int nslots = (int)b->slot_a.size();
   const int tiles = ny * (nx / kTileX);
@@ -931,7 +960,8 @@ os3d_status backward_impl(const os3d_bank* b, const void* U, int udtype, int bat
 
 os3d_status forward_impl(const os3d_bank* b, const float* f, int batch, void* U, int udtype,
                          void* ws, cudaStream_t s) {
-  const Work w = carve(b, ws);
+  Work w;
+  if (const os3d_status e = workspace_for(b, ws, &w)) return e;
   const int nz = b->dims[0], ny = b->dims[1], nx = b->dims[2];
   const int nslots = (int)b->slot_a.size();
   const int tiles = ny * (nx / kTileX);
@@ -968,7 +998,8 @@ os3d_status forward_impl(const os3d_bank* b, const float* f, int batch, void* U,
 // inverse; the score itself is never stored.
 os3d_status upsilon_impl(const os3d_bank* b, const float* f, int batch, float* fout, float power,
                          void* ws, cudaStream_t s) {
-  const Work w = carve(b, ws);
+  Work w;
+  if (const os3d_status e = workspace_for(b, ws, &w)) return e;
   const int nz = b->dims[0], ny = b->dims[1], nx = b->dims[2];
   const int nslots = (int)b->slot_a.size();
   const int tiles = ny * (nx / kTileX);
@@ -1060,7 +1091,9 @@ os3d_status os3d_project(const os3d_bank* b, const void* U, os3d_udtype udtype, 
   cudaStream_t s = (cudaStream_t)stream;
   // the reconstructed image lives in the second block intermediate of the
   // workspace, which neither transform touches while it is needed
-  float* fs = reinterpret_cast<float*>(carve(b, ws).T[1]);
+  Work pw;
+  if (const os3d_status e = workspace_for(b, ws, &pw)) return e;
+  float* fs = reinterpret_cast<float*>(pw.T[1]);
   const size_t vb = (size_t)b->n_o * b->nvox * u_elem_bytes(udtype);
   for (int v = 0; v < batch; ++v) {
     st = backward_impl(b, (const char*)U + v * vb, udtype, 1, fs, ws, s, true);
@@ -1142,7 +1175,8 @@ os3d_status os3d_enhance_linear(const os3d_bank* b, const float* f, int batch, f
   }
   e.h = b->h;
   cudaStream_t s = (cudaStream_t)stream;
-  const Work w = carve(b, ws);
+  Work w;
+  if (const os3d_status we = workspace_for(b, ws, &w)) return we;
   e.fh = w.fh;
   e.A = w.A[0];
   e.seg = b->seg;
@@ -1181,8 +1215,10 @@ os3d_status os3d_upsilon(const os3d_bank* b, const float* f, int batch, float* f
 // scratch lives in g_static_scratch below, a file-scope __device__ array of
 // OS3D_STATIC_MAX_VOXELS x 3 complex values (6 MiB) that every GPU which
 // loads this library holds until the process exits. Its device address is
-// looked up once per device, on the first call made with that device
-// current; that first call must therefore come before any stream capture.
+// looked up on the first call made in each CUDA context of a device (the
+// context's unique id is kept with the address, so a context created anew,
+// e.g. after cudaDeviceReset, gets a fresh lookup); that first call must
+// therefore come before any stream capture.
 // ===========================================================================
 namespace {
 
@@ -1193,20 +1229,51 @@ static __device__ __align__(256) float2 g_static_scratch[3 * kStaticMaxVoxels];
 constexpr int kStaticMaxDevices = 64;
 std::mutex g_static_mu;
 void* g_static_ptr[kStaticMaxDevices] = {};
+unsigned long long g_static_ctx[kStaticMaxDevices] = {};   // context id of each address
 
-// device address of g_static_scratch on the current device
+// Unique id (driver API cuCtxGetId, reached through the runtime's entry-point
+// query, so no link against the driver library) of the current context; 0
+// when it cannot be determined.
+unsigned long long current_context_id() {
+  using GetCurrent = int (*)(void**);
+  using GetId = int (*)(void*, unsigned long long*);
+  static GetCurrent get_current = nullptr;
+  static GetId get_id = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* a = nullptr;
+    void* b = nullptr;
+    cudaDriverEntryPointQueryResult qa, qb;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &a, 12000, cudaEnableDefault, &qa) ==
+            cudaSuccess && qa == cudaDriverEntryPointSuccess &&
+        cudaGetDriverEntryPointByVersion("cuCtxGetId", &b, 12000, cudaEnableDefault, &qb) ==
+            cudaSuccess && qb == cudaDriverEntryPointSuccess) {
+      get_current = reinterpret_cast<GetCurrent>(a);
+      get_id = reinterpret_cast<GetId>(b);
+    }
+    cudaGetLastError();
+  });
+  void* ctx = nullptr;
+  unsigned long long id = 0;
+  if (!get_current || !get_id || get_current(&ctx) != 0 || !ctx || get_id(ctx, &id) != 0) return 0;
+  return id;
+}
+
+// device address of g_static_scratch in the current context
 os3d_status static_scratch_address(float2** out) {
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kStaticMaxDevices)
     return OS3D_ECUDA;
+  const unsigned long long ctx = current_context_id();
   std::lock_guard<std::mutex> lk(g_static_mu);
-  if (!g_static_ptr[dev]) {
+  if (!g_static_ptr[dev] || ctx == 0 || g_static_ctx[dev] != ctx) {
     void* p = nullptr;
     if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess || !p) {
       cudaGetLastError();
       return OS3D_ECUDA;
     }
     g_static_ptr[dev] = p;
+    g_static_ctx[dev] = ctx;
   }
   *out = static_cast<float2*>(g_static_ptr[dev]);
   return OS3D_OK;

@@ -6,13 +6,15 @@
 // one per stream: host-to-device copy of the volume, forward transform into a
 // score held in the arena, exact inverse, device-to-host copy of the
 // reconstruction. Completion is signalled by a host function enqueued behind
-// the copy. Wavelet banks are cached per (grid, orientation set); the arena
-// is allocated once at creation, so serving itself allocates no device memory.
-// With use_graphs, the kernel sequence of forward + inverse for one (bank,
-// arena offset) is captured into a CUDA graph the second time that pair
-// occurs (a pair seen once runs with direct launches, so one-off placements
-// pay no capture) and replayed for every later request on the same pair: one
-// launch instead of about fifty.
+// the copy. Wavelet banks are cached per (grid, orientation set), up to a
+// byte budget (least recently used idle banks are destroyed beyond it); the
+// arena is allocated once at creation, so requests allocate no device memory.
+// Placement: every bank keeps a short list of "home" offsets in the arena, the
+// places its earlier requests occupied; a request goes to the first free home
+// of its bank, else first fit (which becomes a new home while the list has
+// room). With use_graphs, the kernel sequence of forward + inverse of a (bank,
+// home) is captured into a CUDA graph on its first use and replayed by every
+// later request placed there: one launch instead of about fifty.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -40,6 +42,18 @@ size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 class Arena {
  public:
   explicit Arena(size_t size) { free_[0] = size; }
+  // [off, off + n) exactly, if it lies inside one free range
+  bool alloc_at(size_t off, size_t n) {
+    auto it = free_.upper_bound(off);
+    if (it == free_.begin()) return false;
+    --it;
+    const size_t s = it->first, len = it->second;
+    if (off < s || off + n > s + len) return false;
+    free_.erase(it);
+    if (off > s) free_[s] = off - s;
+    if (s + len > off + n) free_[off + n] = s + len - (off + n);
+    return true;
+  }
   bool alloc(size_t n, size_t* off) {
     for (auto it = free_.begin(); it != free_.end(); ++it) {
       if (it->second >= n) {
@@ -72,6 +86,8 @@ class Arena {
   std::map<size_t, size_t> free_;
 };
 
+struct BankEntry;
+
 struct Request {
   long long id = 0;
   int dims[3] = {0, 0, 0};
@@ -81,6 +97,7 @@ struct Request {
   Clock::time_point t_submit, t_done;
   size_t off = 0, bytes = 0;
   int slot = -1;
+  BankEntry* bank = nullptr;   // set at admission; its in-flight count covers the request
   bool done = false;
   os3d_status status = OS3D_OK;
 };
@@ -88,7 +105,10 @@ struct Request {
 struct BankEntry {
   os3d_bank* bank = nullptr;
   int n_o = 0;
-  size_t ws_bytes = 0, score_bytes = 0;
+  size_t ws_bytes = 0, footprint = 0, resident = 0;
+  int inflight = 0;                  // admitted requests not yet retired (worker thread)
+  unsigned long long last_use = 0;   // admission counter value of the latest use
+  std::vector<size_t> homes;         // arena offsets whose graphs belong to this bank
 };
 
 struct GraphEntry {
@@ -109,8 +129,9 @@ struct os3d_server {
   std::vector<std::shared_ptr<Request>> slot_req;   // in-flight request per stream slot
   cudaStream_t bank_stream = nullptr;
   std::map<std::tuple<int, int, int, int>, BankEntry> banks;
+  size_t bank_bytes = 0;                 // resident device bytes of the cached banks
+  unsigned long long admissions = 0;
   std::map<std::pair<const os3d_bank*, size_t>, GraphEntry> graphs;   // worker thread only
-  std::map<std::pair<const os3d_bank*, size_t>, int> seen;            // worker thread only
   long long n_done = 0, n_captured = 0, n_replayed = 0;                // under mu
   std::deque<std::shared_ptr<Request>> pending;
   std::map<long long, std::shared_ptr<Request>> all;
@@ -136,11 +157,31 @@ struct os3d_server {
     d->s->done_cv.notify_all();
   }
 
-  size_t footprint(const Request& r, const BankEntry& e) const {
-    const size_t nvox = (size_t)r.dims[0] * r.dims[1] * r.dims[2];
-    const size_t esz = cfg.udtype == OS3D_U_BF16X2 ? 4 : 8;
-    return align_up((size_t)e.n_o * nvox * esz) + 2 * align_up(nvox * sizeof(float)) +
-           align_up(e.ws_bytes);
+  // destroys idle cached banks, least recently used first, until the cache
+  // plus `extra` bytes fits the budget. Worker thread, with mu NOT held:
+  // destroying a bank frees device memory, which may wait for the host
+  // functions of in-flight requests, and those take mu. Banks, their
+  // in-flight counts and the graphs are touched by the worker thread only.
+  void evict_banks(size_t extra, const BankEntry* keep) {
+    while (bank_bytes + extra > cfg.bank_cache_bytes) {
+      auto victim = banks.end();
+      for (auto it = banks.begin(); it != banks.end(); ++it)
+        if (it->second.inflight == 0 && &it->second != keep &&
+            (victim == banks.end() || it->second.last_use < victim->second.last_use))
+          victim = it;
+      if (victim == banks.end()) return;   // the rest is in use
+      for (auto g = graphs.begin(); g != graphs.end();) {
+        if (g->first.first == victim->second.bank) {
+          cudaGraphExecDestroy(g->second.exec);
+          g = graphs.erase(g);
+        } else {
+          ++g;
+        }
+      }
+      os3d_destroy_bank(victim->second.bank);
+      bank_bytes -= victim->second.resident;
+      banks.erase(victim);
+    }
   }
 
   // the bank of (grid, orientation set), made on first use (worker thread only)
@@ -157,7 +198,14 @@ struct os3d_server {
       st = os3d_make_wavelets(r.dims, V.data(), n_o, &params, bank_stream, &e.bank);
       if (st != OS3D_OK) return st;
       e.n_o = n_o;
-      os3d_bank_info(e.bank, &e.ws_bytes, &e.score_bytes);
+      os3d_bank_info(e.bank, &e.ws_bytes, nullptr);
+      os3d_bank_resident_bytes(e.bank, &e.resident);
+      const size_t nvox = (size_t)r.dims[0] * r.dims[1] * r.dims[2];
+      const size_t esz = cfg.udtype == OS3D_U_BF16X2 ? 4 : 8;
+      e.footprint = align_up((size_t)e.n_o * nvox * esz) + 2 * align_up(nvox * sizeof(float)) +
+                    align_up(e.ws_bytes);
+      evict_banks(e.resident, nullptr);
+      bank_bytes += e.resident;
       it = banks.emplace(key, e).first;
     }
     *out = &it->second;
@@ -182,15 +230,8 @@ struct os3d_server {
       return st;
     };
     const auto key = std::make_pair((const os3d_bank*)e.bank, r.off);
-    bool use_graph = false;
-    if (cfg.use_graphs && !os3d::profiling_enabled()) {
-      if (graphs.count(key)) {
-        use_graph = true;
-      } else {
-        if (seen.size() >= 8 * kMaxGraphs) seen.clear();
-        use_graph = seen[key]++ > 0;
-      }
-    }
+    const bool home = std::find(e.homes.begin(), e.homes.end(), r.off) != e.homes.end();
+    const bool use_graph = cfg.use_graphs && home && !os3d::profiling_enabled();
     if (use_graph) {
       auto it = graphs.find(key);
       if (it == graphs.end()) {
@@ -245,6 +286,7 @@ struct os3d_server {
       for (auto& r : slot_req) {
         if (r && r->done) {
           arena->release(r->off, r->bytes);
+          if (r->bank) r->bank->inflight -= 1;
           r.reset();
         }
       }
@@ -276,9 +318,20 @@ struct os3d_server {
           done_cv.notify_all();
           continue;
         }
-        const size_t need = footprint(*r, *e);
+        const size_t need = e->footprint;
         size_t off = 0;
-        if (need > cfg.arena_bytes || !arena->alloc(need, &off)) {
+        bool placed = false;
+        for (size_t h : e->homes)
+          if (arena->alloc_at(h, need)) {
+            off = h;
+            placed = true;
+            break;
+          }
+        if (!placed && need <= cfg.arena_bytes && arena->alloc(need, &off)) {
+          placed = true;
+          if ((int)e->homes.size() < 2 * cfg.max_inflight) e->homes.push_back(off);
+        }
+        if (!placed) {
           if (need > cfg.arena_bytes) {   // can never fit
             pending.pop_front();
             r->status = OS3D_ENOMEM;
@@ -293,6 +346,9 @@ struct os3d_server {
         r->off = off;
         r->bytes = need;
         r->slot = k;
+        r->bank = e;
+        e->inflight += 1;
+        e->last_use = ++admissions;
         slot_req[k] = r;
         lk.unlock();
         st = launch(*r, *e, k);
@@ -322,6 +378,7 @@ os3d_status os3d_server_default_config(os3d_server_config* c) {
   c->max_inflight = 4;
   c->udtype = OS3D_U_C64;
   c->use_graphs = 1;
+  c->bank_cache_bytes = (size_t)4 << 30;
   return OS3D_OK;
 }
 
@@ -331,7 +388,7 @@ os3d_status os3d_server_create(const os3d_server_config* cfg, const os3d_params*
   *out = nullptr;
   if (cfg->arena_bytes < kAlign || cfg->max_inflight < 1 || cfg->max_inflight > 64 ||
       (cfg->udtype != OS3D_U_C64 && cfg->udtype != OS3D_U_BF16X2) ||
-      (cfg->use_graphs != 0 && cfg->use_graphs != 1))
+      (cfg->use_graphs != 0 && cfg->use_graphs != 1) || cfg->bank_cache_bytes == 0)
     return OS3D_EINVAL;
   auto s = std::make_unique<os3d_server>();
   s->cfg = *cfg;

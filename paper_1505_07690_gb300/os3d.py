@@ -35,7 +35,8 @@ class os3d_diffusion(ctypes.Structure):
 
 class os3d_server_config(ctypes.Structure):
     _fields_ = [("arena_bytes", ctypes.c_size_t), ("max_inflight", ctypes.c_int),
-                ("udtype", ctypes.c_int), ("use_graphs", ctypes.c_int)]
+                ("udtype", ctypes.c_int), ("use_graphs", ctypes.c_int),
+                ("bank_cache_bytes", ctypes.c_size_t)]
 
 
 class OS3DError(RuntimeError):
@@ -76,6 +77,7 @@ def lib():
         L.os3d_adjoint.argtypes = [vp, vp, i, i, vp, vp, vp]
         L.os3d_bank_info.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t),
                                      ctypes.POINTER(ctypes.c_size_t)]
+        L.os3d_bank_resident_bytes.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t)]
         L.os3d_bank_coefficients.argtypes = [vp, ctypes.POINTER(d), ctypes.POINTER(d)]
         L.os3d_bank_minv.argtypes = [vp, vp, vp]
         L.os3d_destroy_bank.argtypes = [vp]
@@ -106,7 +108,8 @@ def lib():
                      "os3d_server_destroy", "os3d_octa_orientations",
                      "os3d_approx_reconstruct", "os3d_project", "os3d_soft_threshold",
                      "os3d_upsilon", "os3d_default_diffusion", "os3d_enhance_linear",
-                     "os3d_angular_propagator", "os3d_server_stats"):
+                     "os3d_angular_propagator", "os3d_server_stats",
+                     "os3d_bank_resident_bytes"):
             getattr(L, name).restype = i
         _lib = L
     return _lib
@@ -165,10 +168,17 @@ class Bank:
         self.dims = tuple(dims)
         self.n_o = n_o
         self.params = params
-        ws, sb = ctypes.c_size_t(0), ctypes.c_size_t(0)
-        _check(lib().os3d_bank_info(handle, ctypes.byref(ws), ctypes.byref(sb)), "os3d_bank_info")
+        ws, fp = ctypes.c_size_t(0), ctypes.c_size_t(0)
+        _check(lib().os3d_bank_info(handle, ctypes.byref(ws), ctypes.byref(fp)), "os3d_bank_info")
         self.workspace_bytes = ws.value
-        self.score_bytes = sb.value
+        self.footprint_bytes_per_volume = fp.value
+
+    def resident_bytes(self) -> int:
+        """Device bytes the bank holds now (os3d_bank_resident_bytes)."""
+        n = ctypes.c_size_t(0)
+        _check(lib().os3d_bank_resident_bytes(self.handle, ctypes.byref(n)),
+               "os3d_bank_resident_bytes")
+        return n.value
 
     def __del__(self):
         h = getattr(self, "handle", None)

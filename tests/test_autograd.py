@@ -27,7 +27,8 @@ def M():
 
 def test_gradient_matches_oracle_adjoint_batch8_96(M):
     """8 x 96^3 spline-tube volumes, 42 orientations, L = 16: the autograd
-    gradient equals the oracle's Re W^*(2 w U) on sampled volumes."""
+    gradient equals the oracle's Re W^*(2 w U) on every volume of the batch
+    (relative L2 <= 1e-5, element-wise <= 2e-5 of the largest value)."""
     import torch
     from paper_1505_07690_gb300.autograd import orientation_score
     dims = (96, 96, 96)
@@ -42,11 +43,11 @@ def test_gradient_matches_oracle_adjoint_batch8_96(M):
     torch.cuda.synchronize()
     g = ft.grad.cpu().numpy()
     del U, loss, wt
-    ob = O.Bank(dims, O.icosa_orientations(1), O.Params(L=16))
-    for b in (0, 5):
-        Uo = O.forward(f[b], ob)
-        go = O.adjoint(2.0 * w[b].astype(np.float64) * Uo, ob)
-        assert rel(g[b], go) <= TOL, b
+    from _oracle_pool import adjoint_of_weighted_score, oracle_map
+    ref = oracle_map(adjoint_of_weighted_score, [(f[b], w[b], dims, 1, 16) for b in range(8)])
+    for b in range(8):
+        assert rel(g[b], ref[b]) <= TOL, b
+        assert np.abs(g[b] - ref[b]).max() <= 2e-5 * np.abs(ref[b]).max(), b
 
 
 def test_gradient_against_fp64_central_differences(M):

@@ -36,3 +36,26 @@ def test_traffic_lookup_follows_the_recorded_hash(tmp_path, monkeypatch):
     assert bench._ncu_traffic("xy_inv_score") == 1234.0
     assert bench._ncu_traffic("z_inv_score") is None     # recorded on other sources
     assert bench._ncu_traffic("xy_fwd_score") is None    # not recorded
+
+
+def test_oracle_on_host_cores_equals_the_oracle():
+    """The bench's multi-process run of the oracle (orientations dealt over
+    spawned single-threaded workers, the orientation sums of M and of the
+    inverse added up from the parts) gives the oracle's own inverse(forward(f))
+    up to the summation order."""
+    import numpy as np
+    from oracle import os3d_oracle as O
+    dims = (8, 10, 12)
+    f = np.random.default_rng(41).standard_normal(dims)
+    V = O.icosa_orientations(1)
+    bank = O.Bank(dims, V, O.Params(L=8))
+    ref = O.inverse(O.forward(f, bank), bank)
+    oc = bench.OracleOnCores(dims, V, 8, f, cores=3)
+    try:
+        assert oc.cores == 3 and sorted(sum(oc.parts, [])) == list(range(len(V)))
+        assert np.abs(oc.bank.M() - bank.M()).max() < 1e-13 * bank.M().max()
+        out, dt = oc.step()
+    finally:
+        oc.close()
+    assert dt > 0
+    assert np.abs(out - ref).max() < 1e-12 * np.abs(ref).max()

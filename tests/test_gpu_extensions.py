@@ -191,6 +191,20 @@ def test_upsilon_equals_the_composition(M):
     assert rel(fu, fc) <= TOL
 
 
+def test_upsilon_64_cubed_162_orientations_p15(M):
+    """The fused Upsilon with p = 1.5 on the whole 64^3 x 162 grid (the
+    162-orientation set, 81 pairs in blocks of 11) against the oracle's
+    W^{*,ext} Phi W f, element by element."""
+    dims = (64, 64, 64)
+    f = synth.spline_tubes(dims, 6, seed=62, noise=0.2)
+    bank, _ = _pair(M, dims, M.os3d_icosa_orientations(2), L=16)
+    fu = _np(M.os3d_upsilon(bank, _cuda(f), 1.5))
+    from _oracle_pool import oracle_map, upsilon_of
+    ref = oracle_map(upsilon_of, [(f, dims, 2, 16, 1.5)])[0]
+    assert rel(fu, ref) <= TOL
+    assert np.abs(fu - ref).max() <= 2e-5 * np.abs(ref).max()
+
+
 def test_upsilon_headline_size_properties(M):
     """128^3 spline tubes, 162 orientations, L = 16 (the benchmark's grid):
     with p = 1 Upsilon is exactly the ball projection IDFT[1_ball f_hat];

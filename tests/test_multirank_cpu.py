@@ -29,7 +29,8 @@ rank = dist.get_rank()
 m = bench._max_over_ranks(1.5 + rank, "cpu")
 print(json.dumps({"rank": rank, "max": m}), flush=True)
 dist.barrier()
-sys.argv = ["bench.py", "--impl", "reference", "--gpus", "2", "--steps", "1", "--warmup", "0"]
+sys.argv = ["bench.py", "--impl", "reference", "--gpus", "2", "--steps", "1", "--warmup", "0",
+            "--workload", "tubes32_no42"]
 rc = bench.main()
 dist.barrier()
 dist.destroy_process_group()
@@ -61,3 +62,5 @@ def test_two_ranks_max_and_reference_arm():
     ref = outs[0][1]
     assert ref["impl"] == "reference" and ref["n_gpus"] == 2 and ref["value"] > 0
     assert ref["e2e"]["h2d_bytes_per_step"] == 0 and ref["cpu_baseline"]["kind"] == "oracle"
+    assert ref["config"]["workload"] == "tubes32_no42" and ref["config"]["n_o"] == 42
+    assert ref["cpu_baseline"]["cores"] == min(os.cpu_count(), 42)

@@ -95,7 +95,7 @@ def test_admission_by_footprint_and_bounded_wait(M):
 
 
 def test_graph_replay_matches_direct_launches(M):
-    """Repeated requests replay the captured graph of their (bank, arena
+    """Repeated requests replay the captured graph of their (bank, home
     offset); results equal those of a server launching directly."""
     vols = _volumes()
     outs = {}
@@ -115,10 +115,10 @@ def test_graph_replay_matches_direct_launches(M):
         assert stats[0] == 3 * len(MIX)
         if graphs:
             # one stream slot and one request at a time: every request lands at
-            # offset 0; each bank runs directly the first time, is captured the
-            # second time and replayed the third
+            # offset 0, the home of every bank; each bank is captured on its
+            # first request and replayed by the second and third
             assert stats[1] == len(set(MIX))
-            assert stats[2] == len(MIX)
+            assert stats[2] == 2 * len(MIX)
         else:
             assert stats[1] == 0 and stats[2] == 0
     for a, b in zip(outs[1], outs[0]):
@@ -146,3 +146,45 @@ def test_graph_replay_with_bf16_scores_and_streams(M):
         assert stats[0] == 3 * len(MIX)
     for a, b in zip(outs[1], outs[0]):
         assert np.array_equal(a, b)
+
+
+def test_homes_give_replays_in_a_concurrent_mix(M):
+    """Requests of a few banks arriving together: each bank's requests go back
+    to the arena offsets its earlier requests used, so after the first round
+    most requests replay a captured graph."""
+    vols = _volumes()
+    ref = _direct(M, vols)
+    srv = M.Server(M.os3d_server_default_config(arena_bytes=2 << 30, max_inflight=3),
+                   M.os3d_default_params(L=12))
+    try:
+        res = []
+        for _ in range(6):
+            tickets = [srv.submit(v, sub) for (d, sub), v in zip(MIX, vols)]
+            res.append([srv.wait(t, 60.0)[0].numpy().copy() for t in tickets])
+        done, captured, replayed = srv.stats()
+    finally:
+        srv.close()
+    assert done == 6 * len(MIX)
+    assert replayed >= 4 * len(MIX)
+    for r in res:
+        for a, b in zip(r, ref):
+            assert rel(a, b) <= TOL
+
+
+def test_bank_cache_budget_evicts_idle_banks(M):
+    """With a bank budget smaller than any bank, every new bank evicts the idle
+    ones; requests alternating between grids still return the direct results
+    (evicted banks are rebuilt on their next use)."""
+    vols = _volumes()
+    ref = _direct(M, vols)
+    srv = M.Server(M.os3d_server_default_config(arena_bytes=2 << 30, max_inflight=2,
+                                                bank_cache_bytes=1),
+                   M.os3d_default_params(L=12))
+    try:
+        for _ in range(2):
+            tickets = [srv.submit(v, sub) for (d, sub), v in zip(MIX, vols)]
+            out = [srv.wait(t, 60.0)[0].numpy().copy() for t in tickets]
+            for a, b in zip(out, ref):
+                assert rel(a, b) <= TOL
+    finally:
+        srv.close()

@@ -60,3 +60,45 @@ def test_static_scratch_rejects_larger_volumes(M):
     st = L.os3d_forward_static(bank.handle, ctypes.c_void_p(f.data_ptr()), 1,
                                ctypes.c_void_p(U.data_ptr()), 0, None)
     assert st == 1   # OS3D_EINVAL: larger than the static scratch
+
+
+@pytest.mark.parametrize("bf16", [False, True])
+def test_static_scratch_forward_on_a_pencil_grid_against_the_oracle(M, bf16):
+    """A 32 x 48 x 64 grid (non-square planes: the pencil passes, including
+    the in-place y pass on the static scratch), through the Python wrapper,
+    complex64 and BF16 scores, against the FP64 oracle; two calls in a row."""
+    import torch
+    from oracle import os3d_oracle as O
+    dims = (32, 48, 64)
+    f = synth.straight_tubes(dims, 3, seed=23, noise=0.1)
+    bank = M.os3d_make_wavelets(dims, M.os3d_icosa_orientations(1), M.os3d_default_params(L=12))
+    Uo = O.forward(f, O.Bank(dims, O.icosa_orientations(1), O.Params(L=12)))
+    fd = torch.from_numpy(f).cuda()
+    for _ in range(2):
+        U = M.os3d_forward_static(bank, fd, bf16=bf16)
+        torch.cuda.synchronize()
+        if bf16:
+            Ug = U.float().cpu().numpy()[0]
+            Ug = Ug[..., 0] + 1j * Ug[..., 1]
+        else:
+            Ug = U.cpu().numpy()[0]
+        assert rel(Ug, Uo) <= (5e-3 if bf16 else TOL)
+        assert np.abs(Ug - Uo).max() <= (1e-2 if bf16 else 2e-5) * np.abs(Uo).max()
+
+
+def test_static_scratch_forward_keeps_no_device_memory(M):
+    """After the first call (which may load the library's device code and
+    with it the static array), further calls leave the device's free memory
+    unchanged: the entry point holds no allocation of its own."""
+    import torch
+    dims = (64, 64, 64)
+    bank = M.os3d_make_wavelets(dims, M.os3d_icosa_orientations(1), M.os3d_default_params(L=12))
+    f = torch.from_numpy(synth.straight_tubes(dims, 3, seed=24)).cuda()
+    U = M.new_score(bank, 1)
+    M.os3d_forward_static(bank, f, U)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for _ in range(3):
+        M.os3d_forward_static(bank, f, U)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
