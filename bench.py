@@ -57,6 +57,9 @@ def _args():
     ap.add_argument("--precision", action="store_true",
                     help="instead of the headline: reconstruction error of complex64 and BF16 "
                          "scores at 256^3 x 42 against the exact result")
+    ap.add_argument("--only-step", action="store_true",
+                    help="time the headline step alone (no end-to-end, per-kernel, operation, "
+                         "serving, precision or CPU legs): for profiler captures")
     ap.add_argument("--workload", default=WORKLOAD,
                     help="named synthetic workload (default: the 128^3 x 162 headline)")
     return ap.parse_args()
@@ -519,6 +522,17 @@ def run_ours(args):
     step_ms = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
     total_ms = _max_over_ranks(ev[0].elapsed_time(ev[-1]), "cuda")
     value = world * nvox * n_o * args.steps / (total_ms / 1e3)
+    if args.only_step:
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                              "steps": args.steps, "warmup": args.warmup,
+                              "ms_per_step": total_ms / args.steps, "only_step": True,
+                              "config": _config(dims, n_o, w["L"], "bf16x2" if args.bf16 else "c64",
+                                                world),
+                              "gpu_launches": launches, "clocks": clk}), flush=True)
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return 0
 
     # ---- end to end: host buffers through the public API, copies timed.
     # Every step copies its input host -> device and its result device -> host

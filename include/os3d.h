@@ -39,6 +39,9 @@
  * synchronises its own stream once (it copies the fitted coefficients back).
  * Errors: every entry point returns an os3d_status; arguments are checked
  * before any launch; nothing aborts or throws across the ABI.
+ * Alignment: the device buffers of the transform calls (images, scores,
+ * gradients) must start on 16-byte boundaries (EINVAL otherwise); the kernels
+ * move two adjacent complex values per access.
  * Devices: a bank belongs to the device that was current at its creation;
  * calls on it must be made with that device current.
  * Concurrency: calls that share a workspace (including the bank's default

@@ -805,6 +805,7 @@ os3d_status check_call(const os3d_bank* b, const void* x, const void* y, int bat
   if (!b || !x || !y || batch < 1) return OS3D_EINVAL;
   if (udtype != OS3D_U_C64 && udtype != OS3D_U_BF16X2) return OS3D_EINVAL;
   if (ws && (reinterpret_cast<uintptr_t>(ws) & 255)) return OS3D_EINVAL;
+  if ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(y)) & 15) return OS3D_EINVAL;
   return current_device_matches(b);
 }
 

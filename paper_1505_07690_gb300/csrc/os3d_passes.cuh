@@ -341,6 +341,18 @@ z_kernel(const __grid_constant__ PassArgs a) {
 // CTAs per plane (NS) and the largest thread count per CTA
 template <int NY, int NX> struct XYSplit { static constexpr int NS = 2, NTMAX = 256; };
 template <> struct XYSplit<256, 256> { static constexpr int NS = 8, NTMAX = 256; };
+// 128^2: a whole plane per CTA (139 KB of shared memory, 512 threads, one CTA
+// per SM): every exchange stays in the CTA, with block barriers instead of
+// cluster barriers
+template <> struct XYSplit<128, 128> { static constexpr int NS = 1, NTMAX = 512; };
+
+// barrier between the phases of a plane: the whole cluster, or for a plane
+// held by one CTA the block
+template <int NS>
+__device__ __forceinline__ void plane_sync() {
+  if constexpr (NS == 1) __syncthreads();
+  else cluster_sync_acqrel();
+}
 
 template <int NY, int NX, int NS = XYSplit<NY, NX>::NS, int NTMAX = XYSplit<NY, NX>::NTMAX>
 struct XYCfg {
@@ -399,7 +411,8 @@ __device__ __forceinline__ float2 load_u(const void* base, long long i) {
 }
 
 template <int NY, int NX, int MODE, int UBF16>
-__global__ void __cluster_dims__(XYSplit<NY, NX>::NS, 1, 1) __launch_bounds__(XYCfg<NY, NX>::NT, 2)
+__global__ void __cluster_dims__(XYSplit<NY, NX>::NS, 1, 1)
+    __launch_bounds__(XYCfg<NY, NX>::NT, XYSplit<NY, NX>::NS == 1 ? 1 : 2)
 xy_kernel(const __grid_constant__ PassArgs a) {
   using C = XYCfg<NY, NX>;
   constexpr int NS = XYSplit<NY, NX>::NS;
@@ -500,7 +513,7 @@ xy_kernel(const __grid_constant__ PassArgs a) {
       }
       // both halves have read their x-layout buffers before either writes into
       // the other's (release/acquire orders these reads before the peer's stores)
-      cluster_sync_acqrel();
+      plane_sync<NS>();
 #pragma unroll
       for (int j = 0; j < C::JX3; ++j) {
         int r, k1;
@@ -515,7 +528,7 @@ xy_kernel(const __grid_constant__ PassArgs a) {
           else st_cluster_f2(peer_base[owner] + 8u * (unsigned)idx, w[j][k2]);
         }
       }
-      cluster_sync_acqrel();   // this CTA's y-layout buffer is complete
+      plane_sync<NS>();   // this CTA's y-layout buffer is complete
     }
     // ---- y direction, step 1 (in place)
     {
@@ -575,7 +588,7 @@ xy_kernel(const __grid_constant__ PassArgs a) {
     }
     __syncthreads();    // work is rewritten by the next x step 1
   }
-  cluster_sync_acqrel();   // no CTA leaves while its peer may still write into it
+  plane_sync<NS>();   // no CTA leaves while its peer may still write into it
 }
 
 // ----------------------------------------------------------------------------
@@ -847,9 +860,10 @@ cudaError_t launch_xy_one(const PassArgs& a, cudaStream_t s) {
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   const int nsl = (MODE == XY_FWD_SCORE || MODE == XY_INV_SCORE) ? a.nslots : 1;
-  // two CTAs per SM, NS per cluster: 2 nsm / NS clusters, looping over units
+  // two CTAs per SM (one for a whole plane per CTA), NS per cluster, looping
+  // over units
   constexpr int NS = XYSplit<NY, NX>::NS;
-  const int clusters = std::max(1, std::min(a.nz * nsl, 2 * nsm / NS));
+  const int clusters = std::max(1, std::min(a.nz * nsl, NS == 1 ? nsm : 2 * nsm / NS));
   k<<<NS * clusters, C::NT, C::smem_bytes, s>>>(a);
   return cudaGetLastError();
 }

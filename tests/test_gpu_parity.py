@@ -210,6 +210,26 @@ def test_workspace_argument(M):
     assert rel(fr, O.inverse(Uo, ob)) <= TOL
 
 
+@pytest.mark.parametrize("bf16,bs,subdiv", [(False, 0, 1), (True, 0, 1), (False, 4, 2), (True, 3, 1)])
+def test_plane_pass_128_squared(M, bf16, bs, subdiv):
+    """128^2 planes take the whole-plane pass (one CTA holds a plane, no
+    cluster): 32 x 128 x 128 against the oracle element by element, c64 and
+    BF16 scores, full and ragged blocks, two calls in a row."""
+    dims = (32, 128, 128)
+    f = synth.spline_tubes(dims, 5, seed=63, noise=0.2)
+    bank, ob = _pair(M, dims, subdiv, L=12, block_slots=bs)
+    Uo = O.forward(f, ob)
+    fo = O.inverse(Uo, ob)
+    fd = _cuda(f)
+    for _ in range(2):
+        U = M.os3d_forward(bank, fd, bf16=bf16)
+        Ug = _to_np(U.float())[0] if bf16 else _to_np(U)[0]
+        if bf16:
+            Ug = Ug[..., 0] + 1j * Ug[..., 1]
+        assert close(Ug, Uo, bf16)
+        assert close(_to_np(M.os3d_inverse(bank, U))[0], fo, bf16)
+
+
 def test_headline_size_sampled(M):
     """128^3 spline tubes, 162 orientations, L = 16, in the benchmark's
     configuration: sampled orientations against the oracle one by one, and
