@@ -231,10 +231,15 @@ os3d_status os3d_angular_propagator(const double* orient, int n, int sh_degree, 
  * host); K Strang steps of dt = t/K (half spatial, angular, half spatial).
  * Because every operator in the cascade commutes with translations, the
  * whole of W^{*,ext} Phi_t W acts on f_hat through one real factor per
- * frequency, which one GPU thread per frequency integrates: the score is never
- * formed and no per-orientation transform runs. Orientation sets of at most 68
- * vectors (EUNSUPPORTED above). Errors: EINVAL (NULL, parameters out of
- * range, dependent harmonics at the requested degree), EUNSUPPORTED, ECUDA. */
+ * frequency: the score is never formed and no per-orientation transform
+ * runs. Sets of at most 68 orientations run the product E v on the CUDA cores
+ * (one GPU thread per frequency and row block); larger sets, up to 176
+ * orientations (the 162 set), on the tensor cores (tcgen05, half-precision
+ * operands split into high and low parts, FP32 accumulation; 128 frequencies
+ * per step of one CTA), with bounded waits counted by os3d_bank_wait_errors.
+ * Errors: EINVAL (NULL, parameters out of range, dependent harmonics at the
+ * requested degree), EUNSUPPORTED (more than 176 orientations, or a workspace
+ * too small for the propagator), ECUDA. */
 os3d_status os3d_enhance_linear(const os3d_bank* bank, const float* f, int batch, float* f_out,
                                 const os3d_diffusion* d, void* workspace, void* stream);
 
@@ -249,6 +254,13 @@ os3d_status os3d_bank_info(const os3d_bank* bank, size_t* workspace_bytes,
  * the in-ball frequency list and, once allocated, its default workspace.
  * Host only. Errors: EINVAL (NULL). */
 os3d_status os3d_bank_resident_bytes(const os3d_bank* bank, size_t* bytes);
+
+/* Bounded waits: the kernels that wait on an mbarrier (the tensor-core
+ * diffusion) give up after 1 s of global time, count the event in a device
+ * counter of the bank and carry on (their results are then invalid).
+ * *count receives the counter (synchronous copy); reset != 0 sets it back to
+ * 0. Errors: EINVAL (NULL, another device current), ECUDA. */
+os3d_status os3d_bank_wait_errors(const os3d_bank* bank, unsigned* count, int reset);
 
 /* Copies of bank data for inspection: the Legendre coefficients b (of A) and
  * c (of h = h_Re + h_Im, normalised), L + 1 doubles each (host); and, on the

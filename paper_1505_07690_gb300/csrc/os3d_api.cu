@@ -104,11 +104,19 @@ struct os3d_bank {
   float* GM = nullptr;                 // G / (n^3 max(M, eps))
   float* Minv = nullptr;               // 1 / max(M, eps), 0 outside the ball
   int4* seg = nullptr;                 // frequencies inside the ball, as row segments
+  unsigned* err = nullptr;             // device counter of bounded waits that ran out
   int nseg = 0, n_in = 0;              // (half of them when every orientation is paired)
   int mirror = 0;
   mutable void* ws = nullptr;          // default workspace, allocated by the first call
                                        // that passes no workspace of its own
   mutable std::mutex ws_mu;
+  // the tensor-core diffusion's propagator in the kernel's layout, for the
+  // last (dt D44, degree) it was computed for
+  mutable std::mutex tc_mu;
+  mutable double tc_tau = -1.0;
+  mutable int tc_degree = -1;
+  mutable float tc_inv_se = 1.f;
+  mutable std::vector<unsigned char> tc_prep;
   cudaStream_t side[2] = {nullptr, nullptr};   // consecutive blocks alternate between these
   cudaEvent_t ev_fork = nullptr, ev_join[2] = {nullptr, nullptr};
   size_t ws_bytes = 0;
@@ -538,10 +546,12 @@ os3d_status os3d_make_wavelets(const int dims[3], const double* orient, int n_o,
   // device allocations
   if (cudaMalloc(&b->Gs, sizeof(float) * b->nvox) != cudaSuccess ||
       cudaMalloc(&b->GM, sizeof(float) * b->nvox) != cudaSuccess ||
-      cudaMalloc(&b->Minv, sizeof(float) * b->nvox) != cudaSuccess) {
+      cudaMalloc(&b->Minv, sizeof(float) * b->nvox) != cudaSuccess ||
+      cudaMalloc(&b->err, sizeof(unsigned)) != cudaSuccess) {
     cudaGetLastError();
     return fail(OS3D_ENOMEM);
   }
+  if (cudaMemsetAsync(b->err, 0, sizeof(unsigned), s) != cudaSuccess) return fail(OS3D_ECUDA);
   {
     bool all_paired = true;
     for (int q : b->slot_b) all_paired = all_paired && q >= 0;
@@ -669,6 +679,15 @@ os3d_status os3d_bank_info(const os3d_bank* b, size_t* ws, size_t* footprint) {
   return OS3D_OK;
 }
 
+os3d_status os3d_bank_wait_errors(const os3d_bank* b, unsigned* count, int reset) {
+  if (!b || !count) return OS3D_EINVAL;
+  if (current_device_matches(b) != OS3D_OK) return OS3D_EINVAL;
+  if (cudaMemcpy(count, b->err, sizeof(unsigned), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return OS3D_ECUDA;
+  if (reset && cudaMemset(b->err, 0, sizeof(unsigned)) != cudaSuccess) return OS3D_ECUDA;
+  return OS3D_OK;
+}
+
 os3d_status os3d_bank_resident_bytes(const os3d_bank* b, size_t* bytes) {
   if (!b || !bytes) return OS3D_EINVAL;
   std::lock_guard<std::mutex> lk(b->ws_mu);
@@ -700,6 +719,7 @@ os3d_status os3d_destroy_bank(os3d_bank* b) {
   if (b->GM) cudaFree(b->GM);
   if (b->Minv) cudaFree(b->Minv);
   if (b->seg) cudaFree(b->seg);
+  if (b->err) cudaFree(b->err);
   if (b->ws) cudaFree(b->ws);
   for (int i = 0; i < 2; ++i) {
     if (b->side[i]) cudaStreamDestroy(b->side[i]);
@@ -1041,6 +1061,67 @@ os3d_status upsilon_impl(const os3d_bank* b, const float* f, int batch, float* f
   return OS3D_OK;
 }
 
+// Linear diffusion with the propagator product on the tensor cores (sets of
+// more than kMaxOrientE orientations): E and the orientations go to the
+// device in the kernel's layout (in the workspace's second block
+// intermediate, which the enhancement does not otherwise use).
+os3d_status enhance_tensor(const os3d_bank* b, const float* f, int batch, float* f_out,
+                           const os3d_diffusion* d, double tau, void* ws, cudaStream_t s) {
+  Work w;
+  if (const os3d_status we = workspace_for(b, ws, &w)) return we;
+  const int np = tc_padded_orientations(b->n_o);
+  EnhanceTCArgs e{};
+  unsigned char* dprep = reinterpret_cast<unsigned char*>(w.T[1]);
+  {
+    // exp(tau L) in FP64 on the host, prepared once per (tau, degree)
+    std::lock_guard<std::mutex> lk(b->tc_mu);
+    if (b->tc_prep.empty() || b->tc_tau != tau || b->tc_degree != d->sh_degree) {
+      std::vector<double> E;
+      if (angular_propagator(b->orient.data(), b->n_o, d->sh_degree, tau, E) < 0) return OS3D_EINVAL;
+      b->tc_inv_se = tc_prepare(E.data(), b->orient.data(), b->n_o, np, b->tc_prep);
+      b->tc_tau = tau;
+      b->tc_degree = d->sh_degree;
+    }
+    if (b->tc_prep.size() > sizeof(float2) * (size_t)b->nvox * b->block_slots)
+      return OS3D_EUNSUPPORTED;
+    e.inv_se = b->tc_inv_se;
+    OS3D_CK(cudaMemcpyAsync(dprep, b->tc_prep.data(), b->tc_prep.size(), cudaMemcpyHostToDevice, s));
+  }
+  e.fh = w.fh;
+  e.A = w.A[0];
+  e.seg = b->seg;
+  e.prep = dprep;
+  e.err = b->err;
+  e.nseg = b->nseg;
+  e.n_in = b->n_in;
+  e.mirror = b->mirror;
+  e.nz = b->dims[0];
+  e.ny = b->dims[1];
+  e.nx = b->dims[2];
+  e.wz = float(2.0 * kPi / b->dims[0]);
+  e.wy = float(2.0 * kPi / b->dims[1]);
+  e.wx = float(2.0 * kPi / b->dims[2]);
+  e.n3 = float(b->nvox);
+  e.n_o = b->n_o;
+  e.steps = d->steps;
+  e.half_dt = float(0.5 * d->t / d->steps);
+  e.D11 = float(d->D11);
+  e.D33 = float(d->D33);
+  e.h = b->h;
+  for (int v = 0; v < batch; ++v) {
+    os3d_status r = prep_fhat(b, f, v, w, s);
+    if (r != OS3D_OK) return r;
+    OS3D_CK(cudaMemsetAsync(w.A[0], 0, sizeof(float2) * b->nvox, s));
+    if (b->n_in > 0)
+      OS3D_CK(counted_launch(OS3D_KIND_ENHANCE, s, [&] { return launch_enhance_tc(e, b->ev, s); }));
+    r = finish_real(b, w, 1, b->GM, f_out, v, s);
+    if (r != OS3D_OK) return r;
+  }
+  // (an upload from pageable memory is staged before cudaMemcpyAsync returns,
+  // so the host copy of E may go)
+  return OS3D_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1151,8 +1232,10 @@ os3d_status os3d_enhance_linear(const os3d_bank* b, const float* f, int batch, f
   if (!ok(d->t) || !ok(d->D11) || !ok(d->D33) || !ok(d->D44) || d->steps < 1 ||
       d->steps > 4096 || d->sh_degree < 0 || d->sh_degree > 15)
     return OS3D_EINVAL;
-  if (b->n_o > kMaxOrientE) return OS3D_EUNSUPPORTED;
+  const bool tensor = b->n_o > kMaxOrientE;
+  if (tensor && tc_padded_orientations(b->n_o) < 0) return OS3D_EUNSUPPORTED;
   const double dt = d->t / d->steps;
+  if (tensor) return enhance_tensor(b, f, batch, f_out, d, dt * d->D44, ws, (cudaStream_t)stream);
   std::vector<double> E;
   if (angular_propagator(b->orient.data(), b->n_o, d->sh_degree, dt * d->D44, E) < 0)
     return OS3D_EINVAL;

@@ -127,6 +127,28 @@ struct EnhanceArgs {
   HEval h;
 };
 cudaError_t launch_enhance(const EnhanceArgs& a, int ev, cudaStream_t s);
+// The same integration with the propagator product on the tensor cores
+// (os3d_diffusion_tc.cu), for orientation sets of up to 176 vectors.
+struct EnhanceTCArgs {
+  const float2* fh;           // f_hat G / n^3
+  float2* A;                  // out: fh * n^3 h^T E h (zero on entry outside the listed frequencies)
+  const int4* seg;            // in-ball row segments {z, y, kx0, first index}
+  const unsigned char* prep;  // E_hi | E_lo (canonical layout, half) | orientations (NP x 3 float)
+  unsigned* err;              // bounded waits that ran out (device counter, or null)
+  int nseg, n_in, mirror;
+  int nz, ny, nx;
+  float wz, wy, wx, n3;
+  int n_o, steps;
+  float half_dt, D11, D33;
+  float inv_se;               // 1 / (the power of two E was scaled by)
+  HEval h;
+};
+cudaError_t launch_enhance_tc(const EnhanceTCArgs& a, int ev, cudaStream_t s);
+int tc_padded_orientations(int n_o);   // N_o padded to the kernel's size, or -1
+size_t tc_prep_bytes(int np);
+// E (n x n FP64) and the orientations in the kernel's device layout; returns
+// the factor that undoes the power-of-two scale applied to E
+float tc_prepare(const double* E, const double* orient, int n, int np, std::vector<unsigned char>& out);
 // host: the frequencies inside the ball |w| < pi (a superset by 1e-12 in
 // |w|^2) as row segments {z, y, kx0, first index}: rows of constant (kz, ky)
 // with kx in [kx0, -kx0] (or [0, a] for the row through the origin when

@@ -78,6 +78,7 @@ def lib():
         L.os3d_bank_info.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t),
                                      ctypes.POINTER(ctypes.c_size_t)]
         L.os3d_bank_resident_bytes.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t)]
+        L.os3d_bank_wait_errors.argtypes = [vp, ctypes.POINTER(ctypes.c_uint), i]
         L.os3d_bank_coefficients.argtypes = [vp, ctypes.POINTER(d), ctypes.POINTER(d)]
         L.os3d_bank_minv.argtypes = [vp, vp, vp]
         L.os3d_destroy_bank.argtypes = [vp]
@@ -109,7 +110,7 @@ def lib():
                      "os3d_approx_reconstruct", "os3d_project", "os3d_soft_threshold",
                      "os3d_upsilon", "os3d_default_diffusion", "os3d_enhance_linear",
                      "os3d_angular_propagator", "os3d_server_stats",
-                     "os3d_bank_resident_bytes"):
+                     "os3d_bank_resident_bytes", "os3d_bank_wait_errors"):
             getattr(L, name).restype = i
         _lib = L
     return _lib
@@ -172,6 +173,13 @@ class Bank:
         _check(lib().os3d_bank_info(handle, ctypes.byref(ws), ctypes.byref(fp)), "os3d_bank_info")
         self.workspace_bytes = ws.value
         self.footprint_bytes_per_volume = fp.value
+
+    def wait_errors(self, reset: bool = True) -> int:
+        """Bounded waits that ran out in this bank's kernels (os3d_bank_wait_errors)."""
+        n = ctypes.c_uint(0)
+        _check(lib().os3d_bank_wait_errors(self.handle, ctypes.byref(n), 1 if reset else 0),
+               "os3d_bank_wait_errors")
+        return n.value
 
     def resident_bytes(self) -> int:
         """Device bytes the bank holds now (os3d_bank_resident_bytes)."""

@@ -276,8 +276,53 @@ def test_enhance_linear_batch_and_identity(M):
     assert rel(_np(M.os3d_enhance_linear(bank, _cuda(f[0]), d0)), fb) <= TOL
 
 
+def _icosa162_minus(k):
+    """The 162 set without its last k antipodal pairs (162 - 2k orientations)."""
+    V = O.icosa_orientations(2)
+    return np.vstack([V[:81 - k], V[81:162 - k]])
+
+
+# more than 68 orientations: the propagator product on the tensor cores, every
+# padded size of that kernel (96, 128, 176 rows) and both wavelet forms
+@pytest.mark.parametrize("make,sub,dims,kw", [
+    (O.icosa_orientations, 2, (32, 32, 32), {}),
+    (O.icosa_orientations, 2, (32, 32, 32), dict(t=2.0, steps=3, D11=0.2, D33=1.0, D44=0.1)),
+    (O.icosa_orientations, 2, (16, 32, 48), dict(t=5.0, steps=6, D11=0.1, D44=0.02)),
+    (lambda k: _icosa162_minus(k), 20, (16, 16, 16), dict(t=2.0, steps=2, D44=0.2)),
+    (lambda k: _icosa162_minus(k), 46, (16, 16, 16), dict(t=1.0, steps=5, D11=0.3, D33=0.6)),
+])
+def test_enhance_linear_tensor_cores_against_oracle(M, make, sub, dims, kw):
+    V = make(sub)
+    assert len(V) > 68
+    bank, ob = _pair(M, dims, V, L=12)
+    d, od = _diff(M, **kw)
+    f = synth.straight_tubes(dims, 3, seed=43, noise=0.1)
+    g = _np(M.os3d_enhance_linear(bank, _cuda(f), d))
+    ref = O.enhance_linear(f, ob, od)
+    assert rel(g, ref) <= TOL
+    assert np.abs(g - ref).max() <= 2e-5 * np.abs(ref).max()
+    assert bank.wait_errors() == 0
+
+
+def test_enhance_linear_tensor_cores_batch_and_repeat(M):
+    """Two volumes per call, two calls: bit-identical repeats (fixed
+    accumulation order on the tensor cores) and parity for both volumes."""
+    dims = (32, 32, 32)
+    bank, ob = _pair(M, dims, O.icosa_orientations(2), L=16)
+    f = np.stack([synth.spline_tubes(dims, 4, seed=s) for s in (44, 45)])
+    d, od = _diff(M, t=3.0, steps=4, D11=0.1, D44=0.05)
+    g1 = _np(M.os3d_enhance_linear(bank, _cuda(f), d))
+    g2 = _np(M.os3d_enhance_linear(bank, _cuda(f), d))
+    assert np.array_equal(g1, g2)
+    for v in range(2):
+        assert rel(g1[v], O.enhance_linear(f[v], ob, od)) <= TOL
+    assert bank.wait_errors() == 0
+
+
 def test_enhance_linear_rejects_large_orientation_sets(M):
-    bank, _ = _pair(M, (16, 16, 16), O.icosa_orientations(2), L=8)
+    """Sets above 176 orientations (the 258-vector octahedral set) are not
+    supported by either kernel."""
+    bank, _ = _pair(M, (16, 16, 16), O.octa_orientations(3), L=8)
     with pytest.raises(M.OS3DError) as e:
         M.os3d_enhance_linear(bank, _cuda(np.zeros((16, 16, 16), np.float32)))
     assert e.value.status == 5
