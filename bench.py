@@ -60,6 +60,9 @@ def _args():
     ap.add_argument("--only-step", action="store_true",
                     help="time the headline step alone (no end-to-end, per-kernel, operation, "
                          "serving, precision or CPU legs): for profiler captures")
+    ap.add_argument("--only-op", default="", choices=["", "enhance_linear_162"],
+                    help="time one operation alone on the headline grid (for profiler captures): "
+                         "enhance_linear_162 = the linear diffusion with the 162-orientation bank")
     ap.add_argument("--workload", default=WORKLOAD,
                     help="named synthetic workload (default: the 128^3 x 162 headline)")
     return ap.parse_args()
@@ -679,6 +682,30 @@ def run_ours(args):
         "kernel_ms": k_ms, "bound": "alu", "kernel_tflops": flops / (k_ms / 1e3) / 1e12,
         "fp32_peak_tflops": fp32_peak,
         "frac_fp32": flops / (k_ms / 1e3) / 1e12 / fp32_peak}
+    del bank42
+    # the same flow for the 162-orientation headline bank: the propagator
+    # product on the tensor cores (128 frequencies per MMA tile, 162 padded to
+    # 176, three half-precision products per step for FP32 accuracy)
+    os3d.os3d_profile_reset()
+    os3d.os3d_profile_enable(True)
+    ms_e2 = timed(lambda: os3d.os3d_enhance_linear(bank, f, dif, fu), args.steps)
+    torch.cuda.synchronize()
+    os3d.os3d_profile_enable(False)
+    pe2 = os3d.os3d_profile_read()["enhance_linear"]
+    k2 = pe2[1] / max(pe2[0], 1)
+    half_ball = (inball + 1) // 2
+    np_pad = 176
+    tiles = (half_ball + 127) // 128
+    mma_flops = tiles * dif.steps * 3 * 2 * 128 * np_pad * np_pad
+    algo162 = half_ball * (dif.steps * 2 * n_o * n_o)
+    ops["enhance_linear_162"] = {
+        "ms": ms_e2, "n_o": n_o, "steps": dif.steps, "kernel_ms": k2,
+        "value": nvox * n_o / (ms_e2 / 1e3), "unit": UNIT,
+        "bound": "tensor", "tensor_tflops": mma_flops / (k2 / 1e3) / 1e12,
+        "peak_tflops": peaks.get("bf16_tflops"), "peak_kind": "measured dense bf16 (f16 runs at the same rate), burst",
+        "frac_tensor": mma_flops / (k2 / 1e3) / 1e12 / peaks.get("bf16_tflops", 1963.0),
+        "fp32_equivalent_tflops": algo162 / (k2 / 1e3) / 1e12,
+        "wait_errors": bank.wait_errors()}
 
     # BF16 storage of the score on the same workload (precision form)
     Ub = os3d.new_score(bank, 1, bf16=True)
@@ -902,12 +929,42 @@ def precision_leg(steps, warmup):
     return line
 
 
+def run_only_op(args):
+    """One operation alone, W warm-up and K timed calls, CUDA events."""
+    import numpy as np
+    import torch
+    from paper_1505_07690_gb300 import build, os3d, synth
+    build.build()
+    w = synth.WORKLOADS[WORKLOAD]
+    dims = w["shape"]
+    V = os3d.os3d_icosa_orientations(w["subdiv"])
+    bank = os3d.os3d_make_wavelets(dims, V, os3d.os3d_default_params(L=w["L"]))
+    f = torch.from_numpy(synth.workload_volume(WORKLOAD)).cuda()
+    fu = torch.empty_like(f)
+    dif = os3d.os3d_default_diffusion()
+    for _ in range(max(args.warmup, 1)):
+        os3d.os3d_enhance_linear(bank, f, dif, fu)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(args.steps):
+        os3d.os3d_enhance_linear(bank, f, dif, fu)
+    b.record()
+    torch.cuda.synchronize()
+    print(json.dumps({"op": args.only_op, "workload": WORKLOAD, "n_o": len(V),
+                      "ms": a.elapsed_time(b) / args.steps, "steps": args.steps,
+                      "wait_errors": bank.wait_errors()}), flush=True)
+    return 0
+
+
 def main():
     global WORKLOAD
     args = _args()
     WORKLOAD = args.workload
     if args.impl == "reference":
         return run_reference(args)
+    if args.only_op:
+        return run_only_op(args)
     if args.serve:
         return run_serve(args)
     if args.precision:

@@ -377,6 +377,14 @@ enum {
   OS3D_KIND_COUNT = 12
 };
 
+/* Self-test of the bounded waits (diagnostic): one CTA of 64 threads waits on
+ * an mbarrier with a limit of limit_s seconds (0 < limit_s <= 10); with
+ * arrive != 0 the barrier is completed first, otherwise nothing arrives and
+ * every thread's wait runs out. *timeouts receives the number of threads
+ * whose wait ran out (64 or 0). Synchronous; allocates and frees 4 device
+ * bytes. The context stays usable afterwards. Errors: EINVAL, ENOMEM, ECUDA. */
+os3d_status os3d_wait_selftest(double limit_s, int arrive, unsigned* timeouts);
+
 /* Number of kernels this library has launched in this process. Host only. */
 unsigned long long os3d_launch_count(void);
 

@@ -1421,6 +1421,23 @@ extern "C" {
 
 unsigned long long os3d_launch_count(void) { return g_launches.load(); }
 
+os3d_status os3d_wait_selftest(double limit_s, int arrive, unsigned* timeouts) {
+  if (!timeouts || !(limit_s > 0.0) || limit_s > 10.0) return OS3D_EINVAL;
+  unsigned* d = nullptr;
+  if (cudaMalloc(&d, sizeof(unsigned)) != cudaSuccess) {
+    cudaGetLastError();
+    return OS3D_ENOMEM;
+  }
+  os3d_status st = OS3D_OK;
+  if (cudaMemset(d, 0, sizeof(unsigned)) != cudaSuccess ||
+      launch_wait_selftest((unsigned long long)(limit_s * 1e9), arrive ? 1 : 0, d, nullptr) !=
+          cudaSuccess ||
+      cudaMemcpy(timeouts, d, sizeof(unsigned), cudaMemcpyDeviceToHost) != cudaSuccess)
+    st = OS3D_ECUDA;
+  cudaFree(d);
+  return st;
+}
+
 os3d_status os3d_profile_enable(int on) {
   g_profile.store(on ? 1 : 0);
   return OS3D_OK;

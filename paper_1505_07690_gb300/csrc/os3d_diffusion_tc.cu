@@ -51,12 +51,29 @@ __device__ __forceinline__ bool mbar_try(unsigned bar, unsigned parity) {
       : "memory");
   return ok != 0;
 }
-__device__ __forceinline__ bool mbar_wait_bounded(unsigned bar, unsigned parity) {
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned bar, unsigned parity,
+                                                  unsigned long long limit_ns = 1000000000ull) {
   if (mbar_try(bar, parity)) return true;
   const unsigned long long t0 = gtimer_ns();
   while (!mbar_try(bar, parity))
-    if (gtimer_ns() - t0 > 1000000000ull) return false;
+    if (gtimer_ns() - t0 > limit_ns) return false;
   return true;
+}
+
+// Self-test of the bounded wait: one CTA waits on an mbarrier of its own;
+// with `arrive` thread 0 arrives first (the wait completes), otherwise
+// nothing ever arrives and every thread's wait runs out after limit_ns.
+__global__ void wait_selftest_kernel(unsigned long long limit_ns, int arrive, unsigned* timeouts) {
+  __shared__ __align__(8) unsigned long long mb;
+  const unsigned bar = smem_addr(&mb);
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (arrive && threadIdx.x == 0)
+    asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+  if (!mbar_wait_bounded(bar, 0, limit_ns)) atomicAdd(timeouts, 1u);
 }
 // shared-memory matrix descriptor, no swizzle: start address, LBO (next core
 // matrix along K), SBO (next 8-row group along M / N), descriptor version 1
@@ -421,6 +438,12 @@ unsigned short half_bits(float x) { return __half_as_ushort(__float2half_rn(x));
 float half_value(unsigned short b) { return __half2float(__ushort_as_half(b)); }
 
 }  // namespace
+
+cudaError_t launch_wait_selftest(unsigned long long limit_ns, int arrive, unsigned* timeouts,
+                                 cudaStream_t s) {
+  wait_selftest_kernel<<<1, 64, 0, s>>>(limit_ns, arrive, timeouts);
+  return cudaGetLastError();
+}
 
 int tc_padded_orientations(int n_o) {
   for (int np : {48, 64, 96, 128, 176})

@@ -145,6 +145,9 @@ struct EnhanceTCArgs {
 };
 cudaError_t launch_enhance_tc(const EnhanceTCArgs& a, int ev, cudaStream_t s);
 int tc_padded_orientations(int n_o);   // N_o padded to the kernel's size, or -1
+// self-test of the bounded mbarrier wait (64 threads, one CTA)
+cudaError_t launch_wait_selftest(unsigned long long limit_ns, int arrive, unsigned* timeouts,
+                                 cudaStream_t s);
 size_t tc_prep_bytes(int np);
 // E (n x n FP64) and the orientations in the kernel's device layout; returns
 // the factor that undoes the power-of-two scale applied to E

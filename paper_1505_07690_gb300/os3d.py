@@ -79,6 +79,7 @@ def lib():
                                      ctypes.POINTER(ctypes.c_size_t)]
         L.os3d_bank_resident_bytes.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t)]
         L.os3d_bank_wait_errors.argtypes = [vp, ctypes.POINTER(ctypes.c_uint), i]
+        L.os3d_wait_selftest.argtypes = [d, i, ctypes.POINTER(ctypes.c_uint)]
         L.os3d_bank_coefficients.argtypes = [vp, ctypes.POINTER(d), ctypes.POINTER(d)]
         L.os3d_bank_minv.argtypes = [vp, vp, vp]
         L.os3d_destroy_bank.argtypes = [vp]
@@ -110,7 +111,7 @@ def lib():
                      "os3d_approx_reconstruct", "os3d_project", "os3d_soft_threshold",
                      "os3d_upsilon", "os3d_default_diffusion", "os3d_enhance_linear",
                      "os3d_angular_propagator", "os3d_server_stats",
-                     "os3d_bank_resident_bytes", "os3d_bank_wait_errors"):
+                     "os3d_bank_resident_bytes", "os3d_bank_wait_errors", "os3d_wait_selftest"):
             getattr(L, name).restype = i
         _lib = L
     return _lib
@@ -427,6 +428,14 @@ def os3d_enhance_linear(bank: Bank, f, diffusion: os3d_diffusion | None = None, 
 
 
 OS3D_KIND_COUNT = 12
+
+
+def os3d_wait_selftest(limit_s: float, arrive: bool) -> int:
+    """Threads of the bounded-wait self-test whose wait ran out (64 or 0)."""
+    n = ctypes.c_uint(0)
+    _check(lib().os3d_wait_selftest(float(limit_s), 1 if arrive else 0, ctypes.byref(n)),
+           "os3d_wait_selftest")
+    return n.value
 
 
 def os3d_launch_count() -> int:

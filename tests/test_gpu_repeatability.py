@@ -71,3 +71,20 @@ def test_plane_cluster_path_256(M):
         M.os3d_inverse(bank, U, r)
         torch.cuda.synchronize()
         assert _same(U, U0) and _same(r, r0)
+
+
+def test_bounded_wait_runs_out_and_the_context_stays_usable(M):
+    """Failure detection without a GPU fault: an mbarrier that nothing
+    completes makes every thread's bounded wait run out (64 reported), a
+    completed one none; afterwards the device still runs transforms."""
+    import time
+    t0 = time.perf_counter()
+    assert M.os3d_wait_selftest(0.05, arrive=False) == 64
+    assert time.perf_counter() - t0 < 5.0
+    assert M.os3d_wait_selftest(0.05, arrive=True) == 0
+    import torch
+    dims = (32, 32, 32)
+    bank = M.os3d_make_wavelets(dims, M.os3d_icosa_orientations(1), M.os3d_default_params(L=12))
+    f = torch.ones((1,) + dims, device="cuda")
+    M.os3d_inverse(bank, M.os3d_forward(bank, f))
+    torch.cuda.synchronize()
