@@ -127,8 +127,8 @@ struct TcLayout {
   static constexpr size_t VBYTES = (size_t)TV * NP * 2; // one half-precision V
   static constexpr size_t OFF_V = 2 * EBYTES;
   static constexpr size_t OFF_NV = 2 * EBYTES + 2 * VBYTES;
-  static constexpr size_t OFF_RED = OFF_NV + sizeof(float) * 3 * NP;    // 2 x 128 floats
-  static constexpr size_t OFF_MISC = OFF_RED + sizeof(float) * 2 * TV;  // tmem slot, mbarrier
+  static constexpr size_t OFF_RED = OFF_NV + sizeof(float) * 3 * NP;    // 4 x 128 floats
+  static constexpr size_t OFF_MISC = OFF_RED + sizeof(float) * 4 * TV;  // tmem slot, 2 mbarriers
   static constexpr size_t BYTES = OFF_MISC + 32;
   static constexpr int TCOLS = 2 * NP <= 32 ? 32 : 2 * NP <= 64 ? 64 : 2 * NP <= 128 ? 128
                              : 2 * NP <= 256 ? 256 : 512;
@@ -183,29 +183,44 @@ __device__ __forceinline__ void tmem_wait(float (&v)[G][16]) {
     for (int j = 0; j < 16; ++j) asm volatile("" : "+f"(v[g][j]));
 }
 
+// Column split of the tile: two MMA groups (columns [0, N0) and [N0, NP),
+// each with its own commit), each served by two warpgroups; four warpgroups
+// on the same 128 lanes, each with a contiguous range of 16-column chunks.
+template <int NP>
+struct TcSplit {
+  static constexpr int NCH = NP / 16;
+  static constexpr int CG0 = (NCH + 1) / 2;            // chunks of MMA group 0
+  static constexpr int N0 = 16 * CG0, N1 = NP - N0;    // columns of the two groups
+  static __host__ __device__ constexpr int begin(int wg) {
+    return wg == 0 ? 0 : wg == 1 ? (CG0 + 1) / 2 : wg == 2 ? CG0 : CG0 + (NCH - CG0 + 1) / 2;
+  }
+  static __host__ __device__ constexpr int end(int wg) { return wg == 3 ? NCH : begin(wg + 1); }
+  static_assert(N1 >= 16, "both MMA groups non-empty");
+};
+
 template <int NP, int EV>
-__global__ void __launch_bounds__(256, 1) enhance_tc_kernel(const __grid_constant__ EnhanceTCArgs a) {
+__global__ void __launch_bounds__(512, 1) enhance_tc_kernel(const __grid_constant__ EnhanceTCArgs a) {
   using L = TcLayout<NP>;
-  constexpr int TV = L::TV, NCH = NP / 16;
-  constexpr int C0 = (NCH + 1) / 2;   // chunks of 16 columns of the first warpgroup
-  constexpr int G = 3;                // chunks loaded per wait
+  using S = TcSplit<NP>;
+  constexpr int TV = L::TV, NCH = NP / 16, NWG = 4;
+  constexpr int G = 1;                // chunks loaded per wait (16 warps hide the latency)
   extern __shared__ __align__(128) unsigned char esm[];
   unsigned char* sEhi = esm;
   unsigned char* sElo = esm + L::EBYTES;
   unsigned char* sVhi = esm + L::OFF_V;
   unsigned char* sVlo = sVhi + L::VBYTES;
   float* nv = reinterpret_cast<float*>(esm + L::OFF_NV);
-  float* red = reinterpret_cast<float*>(esm + L::OFF_RED);   // per-row partials of the two warpgroups
+  float* red = reinterpret_cast<float*>(esm + L::OFF_RED);   // per-row partials of the warpgroups
   unsigned* tslot = reinterpret_cast<unsigned*>(esm + L::OFF_MISC);
-  const unsigned bar = smem_addr(esm + L::OFF_MISC + 16);
-  const int t = threadIdx.x, warp = t >> 5, q = t & (TV - 1), half = t / TV;
-  // both warpgroups serve the same 128 lanes (rows), each half of the columns
-  const int cbeg = half ? C0 : 0, cend = half ? NCH : C0;
+  const unsigned bar0 = smem_addr(esm + L::OFF_MISC + 16), bar1 = bar0 + 8;
+  const int t = threadIdx.x, warp = t >> 5, q = t & (TV - 1), wg = t / TV;
+  const int cbeg = S::begin(wg), cend = S::end(wg);
+  const unsigned my_bar = wg < 2 ? bar0 : bar1;
 
   // E_hi, E_lo (prepared on the host in the canonical layout) and orientations
-  for (size_t o = 16 * (size_t)t; o < 2 * L::EBYTES; o += 16 * 256)
+  for (size_t o = 16 * (size_t)t; o < 2 * L::EBYTES; o += 16 * 512)
     *reinterpret_cast<uint4*>(esm + o) = *reinterpret_cast<const uint4*>(a.prep + o);
-  for (int o = t; o < 3 * NP; o += 256)
+  for (int o = t; o < 3 * NP; o += 512)
     nv[o] = reinterpret_cast<const float*>(a.prep + 2 * L::EBYTES)[o];
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -215,7 +230,8 @@ __global__ void __launch_bounds__(256, 1) enhance_tc_kernel(const __grid_constan
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   if (t == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar1) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -224,15 +240,17 @@ __global__ void __launch_bounds__(256, 1) enhance_tc_kernel(const __grid_constan
   const unsigned tmem = *tslot;
   const unsigned lane_sel = (unsigned)(32 * (warp & 3)) << 16;   // lanes 32 (w % 4) ..
   const unsigned tD = tmem + lane_sel, tF = tmem + lane_sel + NP;
-  constexpr unsigned IDESC = idesc_f16(TV, NP);
+  constexpr unsigned IDESC0 = idesc_f16(TV, S::N0), IDESC1 = idesc_f16(TV, S::N1);
   unsigned phase = 0;
   bool lost = false;
 
-  // max over the row's two halves (one per warpgroup)
-  auto row_max = [&](float m) {
-    red[half * TV + q] = m;
+  // reduction of the row's partial values of the four warpgroups
+  auto row_reduce = [&](float m, bool take_max) {
+    red[wg * TV + q] = m;
     __syncthreads();
-    const float r = fmaxf(red[q], red[TV + q]);
+    float r = red[q];
+#pragma unroll
+    for (int g = 1; g < NWG; ++g) r = take_max ? fmaxf(r, red[g * TV + q]) : r + red[g * TV + q];
     __syncthreads();
     return r;
   };
@@ -306,36 +324,44 @@ __global__ void __launch_bounds__(256, 1) enhance_tc_kernel(const __grid_constan
       tmem_st16(tD + 16 * c, Vv);
     }
     asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-    float sq = row_scale(row_max(vmax));
+    float sq = row_scale(row_reduce(vmax, true));
     split_to_smem(sq);
     float msum = 0.f;
 #pragma unroll 1
     for (int s = 0; s < a.steps; ++s) {
-      // ---- D = V E^T (three products of the split operands), one thread issues
+      // ---- D = V E^T (three products of the split operands) in two column
+      // groups, each completing on its own mbarrier; one thread issues
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncthreads();
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       if (t == 0) {
         const unsigned vh = smem_addr(sVhi), vl = smem_addr(sVlo);
-        const unsigned eh = smem_addr(sEhi), el = smem_addr(sElo);
+#pragma unroll
+        for (int grp = 0; grp < 2; ++grp) {
+          const unsigned eh = smem_addr(sEhi) + (grp ? (S::N0 / 8) * L::SBO : 0u);
+          const unsigned el = smem_addr(sElo) + (grp ? (S::N0 / 8) * L::SBO : 0u);
+          const unsigned dcol = tmem + (grp ? (unsigned)S::N0 : 0u);
+          const unsigned id = grp ? IDESC1 : IDESC0;
 #pragma unroll 1
-        for (int kk = 0; kk < NCH; ++kk)
-          mma_f16(tmem, smem_desc(vh + kk * 2 * L::LBO, L::LBO, L::SBO),
-                  smem_desc(eh + kk * 2 * L::LBO, L::LBO, L::SBO), IDESC, kk > 0);
+          for (int kk = 0; kk < NCH; ++kk)
+            mma_f16(dcol, smem_desc(vh + kk * 2 * L::LBO, L::LBO, L::SBO),
+                    smem_desc(eh + kk * 2 * L::LBO, L::LBO, L::SBO), id, kk > 0);
 #pragma unroll 1
-        for (int kk = 0; kk < NCH; ++kk)
-          mma_f16(tmem, smem_desc(vh + kk * 2 * L::LBO, L::LBO, L::SBO),
-                  smem_desc(el + kk * 2 * L::LBO, L::LBO, L::SBO), IDESC, 1);
+          for (int kk = 0; kk < NCH; ++kk)
+            mma_f16(dcol, smem_desc(vh + kk * 2 * L::LBO, L::LBO, L::SBO),
+                    smem_desc(el + kk * 2 * L::LBO, L::LBO, L::SBO), id, 1);
 #pragma unroll 1
-        for (int kk = 0; kk < NCH; ++kk)
-          mma_f16(tmem, smem_desc(vl + kk * 2 * L::LBO, L::LBO, L::SBO),
-                  smem_desc(eh + kk * 2 * L::LBO, L::LBO, L::SBO), IDESC, 1);
-        asm volatile(
-            "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
-            : "memory");
+          for (int kk = 0; kk < NCH; ++kk)
+            mma_f16(dcol, smem_desc(vl + kk * 2 * L::LBO, L::LBO, L::SBO),
+                    smem_desc(eh + kk * 2 * L::LBO, L::LBO, L::SBO), id, 1);
+          asm volatile(
+              "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                  grp ? bar1 : bar0)
+              : "memory");
+        }
       }
-      if (!mbar_wait_bounded(bar, phase)) lost = true;
+      if (!mbar_wait_bounded(my_bar, phase)) lost = true;
       phase ^= 1u;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       // ---- W = F^2 D (F D after the last step), scales undone
@@ -378,15 +404,14 @@ __global__ void __launch_bounds__(256, 1) enhance_tc_kernel(const __grid_constan
       }
       if (!last) {
         asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-        sq = row_scale(row_max(wmax));
+        sq = row_scale(row_reduce(wmax, true));
         split_to_smem(sq);
       }
     }
-    // m = h^T v: the two warpgroups' partial sums of the row
-    red[half * TV + q] = msum;
-    __syncthreads();
-    if (half == 0 && vox >= 0) {
-      const float m = (red[q] + red[TV + q]) * a.n3;
+    // m = h^T v: the warpgroups' partial sums of the row
+    const float mtot = row_reduce(msum, false);
+    if (wg == 0 && vox >= 0) {
+      const float m = mtot * a.n3;
       const float2 fh = a.fh[vox];
       a.A[vox] = make_float2(fh.x * m, fh.y * m);
       if (mvox >= 0) {
@@ -394,9 +419,8 @@ __global__ void __launch_bounds__(256, 1) enhance_tc_kernel(const __grid_constan
         a.A[mvox] = make_float2(fm.x * m, fm.y * m);
       }
     }
-    __syncthreads();   // red is rewritten by the next tile
   }
-  if (lost && t == 0 && a.err) atomicAdd(a.err, 1u);
+  if (lost && (t & 127) == 0 && a.err) atomicAdd(a.err, 1u);
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 0)
@@ -417,12 +441,12 @@ cudaError_t launch_tc_np(const EnhanceTCArgs& a, cudaStream_t s) {
   int dev = 0, nsm = 0, per_sm = 1;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 256, smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 512, smem);
   if (e != cudaSuccess) return e;
   per_sm = std::max(1, std::min(per_sm, max_ctas));
   const int ntiles = (a.n_in + kTVtc - 1) / kTVtc;
   const int grid = std::max(1, std::min(ntiles, nsm * per_sm));
-  k<<<grid, 256, smem, s>>>(a);
+  k<<<grid, 512, smem, s>>>(a);
   return cudaGetLastError();
 }
 

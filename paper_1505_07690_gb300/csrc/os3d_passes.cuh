@@ -326,25 +326,26 @@ z_kernel(const __grid_constant__ PassArgs a) {
 }
 
 // ----------------------------------------------------------------------------
-// xy-pass on a cluster of NS CTAs (2, or 8 for 256^2 planes). CTA h holds rows
+// xy-pass on NS CTAs per z-plane: one (a whole plane per CTA) for planes up
+// to 128^2, a cluster of 8 for 256^2 planes. CTA h holds rows
 // [h NY/NS, (h+1) NY/NS) of a z-plane for the x direction and columns
 // [h NX/NS, (h+1) NX/NS) for the y direction; the x step-2 outputs go straight
-// into the owner's y-layout buffer (local or distributed shared memory). Half a
-// plane (74 KB at 128^2; an eighth, 84 KB, at 256^2) lets two CTAs share an
-// SM, so one CTA's loads overlap the other's DFTs.
+// into the owner's y-layout buffer (its own shared memory, or for NS > 1
+// distributed shared memory). An eighth of a 256^2 plane (84 KB) lets two
+// CTAs share an SM, so one CTA's loads overlap the other's DFTs.
 // Shared layout: x layout row pitch NX + 8 (rows alternate 64-byte halves of
 // the bank space) with an XOR swizzle inside each group of R2x columns; y
-// layout row pitch NX/2 + 8. All accesses of the 128^2 plan are
-// bank-conflict-free. Work units: (plane, slot) for the score modes, planes
-// for the real modes; clusters loop over units.
+// layout row pitch NX/NS + 8. Work units: (plane, slot) for the score modes,
+// planes for the real modes; CTAs (clusters) loop over units.
 // ----------------------------------------------------------------------------
-// CTAs per plane (NS) and the largest thread count per CTA
-template <int NY, int NX> struct XYSplit { static constexpr int NS = 2, NTMAX = 256; };
+// CTAs per plane (NS) and the largest thread count per CTA. Planes up to
+// 128^2: a whole plane per CTA (up to 139 KB of shared memory and 512
+// threads), so every exchange stays in the CTA, with block barriers instead
+// of cluster barriers (faster than half planes on 2-CTA clusters by 5 % at
+// 128^2 and 7-21 % for the smaller planes). 256^2: an eighth of a plane per
+// CTA on 8-CTA clusters.
+template <int NY, int NX> struct XYSplit { static constexpr int NS = 1, NTMAX = 512; };
 template <> struct XYSplit<256, 256> { static constexpr int NS = 8, NTMAX = 256; };
-// 128^2: a whole plane per CTA (139 KB of shared memory, 512 threads, one CTA
-// per SM): every exchange stays in the CTA, with block barriers instead of
-// cluster barriers
-template <> struct XYSplit<128, 128> { static constexpr int NS = 1, NTMAX = 512; };
 
 // barrier between the phases of a plane: the whole cluster, or for a plane
 // held by one CTA the block
@@ -860,10 +861,16 @@ cudaError_t launch_xy_one(const PassArgs& a, cudaStream_t s) {
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   const int nsl = (MODE == XY_FWD_SCORE || MODE == XY_INV_SCORE) ? a.nslots : 1;
-  // two CTAs per SM (one for a whole plane per CTA), NS per cluster, looping
-  // over units
+  // two CTAs per SM, NS per cluster, looping over units; a whole plane per CTA:
+  // as many CTAs as are resident at once
   constexpr int NS = XYSplit<NY, NX>::NS;
-  const int clusters = std::max(1, std::min(a.nz * nsl, NS == 1 ? nsm : 2 * nsm / NS));
+  int per_sm = 2;
+  if constexpr (NS == 1) {
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, C::NT, C::smem_bytes);
+    if (e != cudaSuccess) return e;
+    per_sm = std::max(1, per_sm);
+  }
+  const int clusters = std::max(1, std::min(a.nz * nsl, NS == 1 ? per_sm * nsm : 2 * nsm / NS));
   k<<<NS * clusters, C::NT, C::smem_bytes, s>>>(a);
   return cudaGetLastError();
 }
