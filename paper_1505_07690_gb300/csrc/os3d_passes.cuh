@@ -607,9 +607,12 @@ xy_kernel(const __grid_constant__ PassArgs a) {
 // T_s.
 // ----------------------------------------------------------------------------
 template <int NY, int NX>
-__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(XYCfg<NY, NX, 2, 256>::NT, 2)
+__global__ void __cluster_dims__(XYSplit<NY, NX>::NS, 1, 1)
+    __launch_bounds__(XYCfg<NY, NX>::NT, XYSplit<NY, NX>::NS == 1 ? 1 : 2)
 xy_soft_kernel(const __grid_constant__ PassArgs a) {
-  using C = XYCfg<NY, NX, 2, 256>;
+  using C = XYCfg<NY, NX>;
+  constexpr int NS = XYSplit<NY, NX>::NS;
+  static_assert(NS <= 2, "a plane on one CTA or on a 2-CTA cluster");
   constexpr int R1x = C::R1x, R2x = C::R2x, R1y = C::R1y, R2y = C::R2y;
   constexpr int NT = C::NT, NYH = C::NYH, NXH = C::NXH;
 
@@ -620,9 +623,9 @@ xy_soft_kernel(const __grid_constant__ PassArgs a) {
 
   const int t = threadIdx.x;
   const int h = (int)cluster_rank();
-  const unsigned peer_base = map_cluster_rank(smem_addr(work), (unsigned)(h ^ 1));
+  const unsigned peer_base = NS == 1 ? 0u : map_cluster_rank(smem_addr(work), (unsigned)(h ^ 1));
   const long long P = (long long)NY * NX;
-  const int cl = blockIdx.x >> 1, ncl = gridDim.x >> 1;
+  const int cl = blockIdx.x / NS, ncl = gridDim.x / NS;
   const int nunits = a.nz * a.nslots;
   // row of the y-layout that holds y index n after the IDFT along y
   auto yrow = [](int n) { return R2y * (n % R1y) + n / R1y; };
@@ -675,7 +678,7 @@ xy_soft_kernel(const __grid_constant__ PassArgs a) {
         for (int m = 0; m < R2x; ++m) w[j][m] = work[C::xphys(r, m + R2x * k1)];
         dft<R2x, +1>(w[j]);
       }
-      cluster_sync_acqrel();   // both halves have read their x layouts
+      plane_sync<NS>();   // both halves have read their x layouts
 #pragma unroll
       for (int j = 0; j < C::JX3; ++j) {
         int r, k1;
@@ -690,7 +693,7 @@ xy_soft_kernel(const __grid_constant__ PassArgs a) {
           else st_cluster_f2(peer_base + 8u * (unsigned)idx, w[j][k2]);
         }
       }
-      cluster_sync_acqrel();   // this CTA's y layout is complete
+      plane_sync<NS>();   // this CTA's y layout is complete
     }
     // ---- (3) IDFT along y, step 1 (in place)
     {
@@ -756,7 +759,7 @@ xy_soft_kernel(const __grid_constant__ PassArgs a) {
         for (int m = 0; m < R2y; ++m) w[j][m] = work[yrow(m + R2y * k1) * C::PY + c];
         dft<R2y, -1>(w[j]);
       }
-      cluster_sync_acqrel();   // both halves have read their y layouts
+      plane_sync<NS>();   // both halves have read their y layouts
 #pragma unroll
       for (int j = 0; j < C::JY3; ++j) {
         const int q = t + NT * j;
@@ -770,7 +773,7 @@ xy_soft_kernel(const __grid_constant__ PassArgs a) {
           else st_cluster_f2(peer_base + 8u * (unsigned)idx, w[j][k2]);
         }
       }
-      cluster_sync_acqrel();   // this CTA's x layout is complete
+      plane_sync<NS>();   // this CTA's x layout is complete
     }
     // ---- (7) DFT along x, step 1 (in place on this CTA's rows)
     {
@@ -808,12 +811,13 @@ xy_soft_kernel(const __grid_constant__ PassArgs a) {
     }
     __syncthreads();    // work is rewritten by the next unit
   }
-  cluster_sync_acqrel();   // no CTA leaves while its peer may still write into it
+  plane_sync<NS>();   // no CTA leaves while its peer may still write into it
 }
 
 template <int NY, int NX>
 cudaError_t launch_xy_soft_one(const PassArgs& a, cudaStream_t s) {
-  using C = XYCfg<NY, NX, 2, 256>;
+  using C = XYCfg<NY, NX>;
+  constexpr int NS = XYSplit<NY, NX>::NS;
   auto k = xy_soft_kernel<NY, NX>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)C::smem_bytes);
@@ -821,8 +825,14 @@ cudaError_t launch_xy_soft_one(const PassArgs& a, cudaStream_t s) {
   int dev = 0, nsm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  const int clusters = std::max(1, std::min(a.nz * a.nslots, nsm));
-  k<<<2 * clusters, C::NT, C::smem_bytes, s>>>(a);
+  int per_sm = 1;
+  if constexpr (NS == 1) {
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, C::NT, C::smem_bytes);
+    if (e != cudaSuccess) return e;
+    per_sm = std::max(1, per_sm);
+  }
+  const int clusters = std::max(1, std::min(a.nz * a.nslots, per_sm * nsm));
+  k<<<NS * clusters, C::NT, C::smem_bytes, s>>>(a);
   return cudaGetLastError();
 }
 
