@@ -125,9 +125,10 @@ os3d_status os3d_octa_orientations(int subdiv, double* out, int capacity, int* n
  * Antipodal pairs in `orient` are detected (|n_i + n_j| < 1e-9) and share
  * one transform in the forward and inverse passes.
  * Supported axis lengths: 16, 32, 48, 64, 96, 128, 160 and 256 on every axis.
- * Square (ny, nx) planes of side <= 128 and 256^2 planes use the fused 2D
- * plane pass (a whole plane per CTA, or for 256^2 an eighth of a plane per
- * CTA on clusters of 8); other planes use separate x and y pencil passes.
+ * Square (ny, nx) planes of side <= 128, 128 x 160 planes and 256^2 planes
+ * use the fused 2D plane pass (a whole plane per CTA, or for 256^2 an eighth
+ * of a plane per CTA on clusters of 8); other planes use separate x and y
+ * pencil passes.
  * Errors: EINVAL (NULL, n_o < 1, a non-unit orientation, parameter out of
  * range), EUNSUPPORTED (grid), ENOMEM, ECUDA. `stream` may be NULL (legacy
  * default stream). */

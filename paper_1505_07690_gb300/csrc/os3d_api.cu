@@ -26,7 +26,7 @@ namespace os3d {
 OS3D_DECL_Z(16) OS3D_DECL_Z(32) OS3D_DECL_Z(48) OS3D_DECL_Z(64) OS3D_DECL_Z(96)
 OS3D_DECL_Z(128) OS3D_DECL_Z(160) OS3D_DECL_Z(256)
 OS3D_DECL_XY(16, 16) OS3D_DECL_XY(32, 32) OS3D_DECL_XY(48, 48) OS3D_DECL_XY(64, 64)
-OS3D_DECL_XY(96, 96) OS3D_DECL_XY(128, 128) OS3D_DECL_XY(256, 256)
+OS3D_DECL_XY(96, 96) OS3D_DECL_XY(128, 128) OS3D_DECL_XY(256, 256) OS3D_DECL_XY(128, 160)
 #define OS3D_DECL_PN(N)                                                                   \
   cudaError_t launch_pencil_##N(int, int, int, const PassArgs&, const PencilGeom&, long long, \
                                 int, cudaStream_t);
@@ -53,11 +53,12 @@ bool z_supported(int nz) {
          nz == 256;
 }
 bool xy_supported(int ny, int nx) {
-  return ny == nx &&
-         (nx == 16 || nx == 32 || nx == 48 || nx == 64 || nx == 96 || nx == 128 || nx == 256);
+  return (ny == nx &&
+          (nx == 16 || nx == 32 || nx == 48 || nx == 64 || nx == 96 || nx == 128 || nx == 256)) ||
+         (ny == 128 && nx == 160);
 }
 // planes the fused soft-threshold plane pass holds (2-CTA clusters)
-bool soft_plane_supported(int ny, int nx) { return xy_supported(ny, nx) && nx <= 128; }
+bool soft_plane_supported(int ny, int nx) { return ny == nx && xy_supported(ny, nx) && nx <= 128; }
 cudaError_t launch_z(int nz, int mode, int ev, const PassArgs& a, int tiles, cudaStream_t s) {
   switch (nz) {
     case 16: return launch_z_16(mode, ev, a, tiles, s);
@@ -72,6 +73,7 @@ cudaError_t launch_z(int nz, int mode, int ev, const PassArgs& a, int tiles, cud
   }
 }
 cudaError_t launch_xy(int ny, int nx, int mode, int ub, const PassArgs& a, cudaStream_t s) {
+  if (ny == 128 && nx == 160) return launch_xy_128_160(mode, ub, a, s);
   if (ny != nx) return cudaErrorInvalidValue;
   switch (nx) {
     case 16: return launch_xy_16_16(mode, ub, a, s);

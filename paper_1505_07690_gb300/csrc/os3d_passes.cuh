@@ -362,8 +362,9 @@ struct XYCfg {
   static constexpr int R1y = Plan<NY>::R1, R2y = Plan<NY>::R2;
   static_assert((R2x & (R2x - 1)) == 0, "R2x must be a power of two");
   static constexpr bool ok(int nt) {
+    // (a rectangular plane may leave the last pass of y step 1 partial)
     return nt % 32 == 0 && (NYH * R2x) % nt == 0 && nt % R2x == 0 && (NYH * R1x) % nt == 0 &&
-           nt % R2y == 0 && NXH % (nt / R2y) == 0 && (NXH * R1y) % nt == 0;
+           nt % R2y == 0 && (NY != NX || NXH % (nt / R2y) == 0) && (NXH * R1y) % nt == 0;
   }
   static constexpr int pick() {
     for (int nt = NTMAX; nt >= 32; nt -= 32)
@@ -378,7 +379,7 @@ struct XYCfg {
   static constexpr int JX1 = NYH * R2x / NT;
   static constexpr int JX3 = NYH * R1x / NT;
   static constexpr int CW = NT / R2y;
-  static constexpr int JY1 = NXH / CW;
+  static constexpr int JY1 = (NXH + CW - 1) / CW;
   static constexpr int JY3 = NXH * R1y / NT;
   static constexpr size_t smem_bytes = sizeof(float2) * (size_t(BUF) + NX + NY);
   static __device__ __forceinline__ int xphys(int r, int x) {
@@ -540,6 +541,7 @@ xy_kernel(const __grid_constant__ PassArgs a) {
 #pragma unroll
       for (int j = 0; j < C::JY1; ++j) {
         const int c = t % C::CW + C::CW * j;
+        if (NXH % C::CW != 0 && c >= NXH) break;
         float2 u1[R1y];
 #pragma unroll
         for (int n1 = 0; n1 < R1y; ++n1) u1[n1] = work[(n2 + R2y * n1) * C::PY + c];
@@ -704,6 +706,7 @@ xy_soft_kernel(const __grid_constant__ PassArgs a) {
 #pragma unroll 1
       for (int j = 0; j < C::JY1; ++j) {
         const int c = t % C::CW + C::CW * j;
+        if (NXH % C::CW != 0 && c >= NXH) break;
         float2 u1[R1y];
 #pragma unroll
         for (int n1 = 0; n1 < R1y; ++n1) u1[n1] = work[(n2 + R2y * n1) * C::PY + c];
@@ -738,6 +741,7 @@ xy_soft_kernel(const __grid_constant__ PassArgs a) {
 #pragma unroll 1
       for (int j = 0; j < C::JY1; ++j) {
         const int c = t % C::CW + C::CW * j;
+        if (NXH % C::CW != 0 && c >= NXH) break;
         float2 u1[R1y];
 #pragma unroll
         for (int n1 = 0; n1 < R1y; ++n1) u1[n1] = work[yrow(n2 + R2y * n1) * C::PY + c];

@@ -258,6 +258,23 @@ def test_pencil_path_grids(M, dims, subdiv):
     _check_forward_inverse(M, dims, f, subdiv=subdiv, L=12, block_slots=4)
 
 
+@pytest.mark.parametrize("bf16", [False, True])
+def test_plane_pass_rectangular_128x160(M, bf16):
+    """128 x 160 planes (the serving mix's 96 x 128 x 160 grid) take the
+    whole-plane pass with a partial last pass of columns in the y direction;
+    16 x 128 x 160 against the oracle element by element, ragged blocks."""
+    dims = (16, 128, 160)
+    f = synth.spline_tubes(dims, 4, seed=64, noise=0.2)
+    bank, ob = _pair(M, dims, 1, L=12, block_slots=4)
+    U = M.os3d_forward(bank, _cuda(f), bf16=bf16)
+    Ug = _to_np(U.float())[0] if bf16 else _to_np(U)[0]
+    if bf16:
+        Ug = Ug[..., 0] + 1j * Ug[..., 1]
+    Uo = O.forward(f, ob)
+    assert close(Ug, Uo, bf16)
+    assert close(_to_np(M.os3d_inverse(bank, U))[0], O.inverse(Uo, ob), bf16)
+
+
 def test_precision_workload_sampled_c64_and_bf16(M):
     """256^3, 40 spline tubes, 42 orientations, L = 20: complex64 scores match
     the oracle on sampled orientations; both storage formats reconstruct
