@@ -60,9 +60,10 @@ def _args():
     ap.add_argument("--only-step", action="store_true",
                     help="time the headline step alone (no end-to-end, per-kernel, operation, "
                          "serving, precision or CPU legs): for profiler captures")
-    ap.add_argument("--only-op", default="", choices=["", "enhance_linear_162"],
+    ap.add_argument("--only-op", default="", choices=["", "enhance_linear_162", "upsilon"],
                     help="time one operation alone on the headline grid (for profiler captures): "
-                         "enhance_linear_162 = the linear diffusion with the 162-orientation bank")
+                         "enhance_linear_162 = the linear diffusion with the 162-orientation bank; "
+                         "upsilon = the fused soft-threshold processing (p = 1.5)")
     ap.add_argument("--workload", default=WORKLOAD,
                     help="named synthetic workload (default: the 128^3 x 162 headline)")
     return ap.parse_args()
@@ -942,13 +943,17 @@ def run_only_op(args):
     f = torch.from_numpy(synth.workload_volume(WORKLOAD)).cuda()
     fu = torch.empty_like(f)
     dif = os3d.os3d_default_diffusion()
+    if args.only_op == "upsilon":
+        op = lambda: os3d.os3d_upsilon(bank, f, 1.5, fu)
+    else:
+        op = lambda: os3d.os3d_enhance_linear(bank, f, dif, fu)
     for _ in range(max(args.warmup, 1)):
-        os3d.os3d_enhance_linear(bank, f, dif, fu)
+        op()
     torch.cuda.synchronize()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     a.record()
     for _ in range(args.steps):
-        os3d.os3d_enhance_linear(bank, f, dif, fu)
+        op()
     b.record()
     torch.cuda.synchronize()
     print(json.dumps({"op": args.only_op, "workload": WORKLOAD, "n_o": len(V),
