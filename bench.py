@@ -60,7 +60,7 @@ def _args():
     ap.add_argument("--only-step", action="store_true",
                     help="time the headline step alone (no end-to-end, per-kernel, operation, "
                          "serving, precision or CPU legs): for profiler captures")
-    ap.add_argument("--only-op", default="", choices=["", "enhance_linear_162", "upsilon"],
+    ap.add_argument("--only-op", default="", choices=["", "enhance_linear_162", "upsilon", "autograd"],
                     help="time one operation alone on the headline grid (for profiler captures): "
                          "enhance_linear_162 = the linear diffusion with the 162-orientation bank; "
                          "upsilon = the fused soft-threshold processing (p = 1.5)")
@@ -434,7 +434,7 @@ def _autograd_step(os3d, synth, steps, timed):
     torch.autograd."""
     import numpy as np
     import torch
-    from paper_1505_07690_gb300.autograd import orientation_score
+    from paper_1505_07690_gb300.autograd import orientation_score, score_energy, weighted_energy
     w = synth.WORKLOADS["splines96x8_no42"]
     dims, B = w["shape"], w["batch"]
     V = os3d.os3d_icosa_orientations(w["subdiv"])
@@ -443,12 +443,27 @@ def _autograd_step(os3d, synth, steps, timed):
                                    for b in range(B)])).cuda().requires_grad_(True)
     wt = torch.from_numpy(synth.score_weights((B, len(V)) + tuple(dims), seed=1)).cuda()
 
-    def step():
+    def step_torch_loss():
         f.grad = None
         U = orientation_score(f, bank)
         (wt * (U.real ** 2 + U.imag ** 2)).sum().backward()
 
+    def step_energy():
+        f.grad = None
+        weighted_energy(orientation_score(f, bank), wt).backward()
+
+    def step():
+        f.grad = None
+        score_energy(f, bank, wt).backward()
+
+    ms_torch = timed(step_torch_loss, max(2, steps // 2))
+    ms_energy = timed(step_energy, max(2, steps // 2))
+    os3d.os3d_profile_reset()
+    os3d.os3d_profile_enable(True)
     ms = timed(step, max(2, steps // 2))
+    torch.cuda.synchronize()
+    os3d.os3d_profile_enable(False)
+    prof = os3d.os3d_profile_read()
     fd = f.detach()
     U = os3d.new_score(bank, B)
     g = torch.empty_like(fd)
@@ -461,8 +476,20 @@ def _autograd_step(os3d, synth, steps, timed):
     vo = B * int(np.prod(dims)) * len(V)
     del f, wt, U, g, fd
     torch.cuda.empty_cache()
+    # the energy kernel streams the score and the weights: 12 bytes per
+    # complex element (the weighted adjoint reads the same 12 bytes in its
+    # plane pass instead of an 8-byte stored gradient)
+    n, tot = prof["weighted_energy"]
+    k_ms = tot / max(n, 1)
+    ek = {"kernel_ms": k_ms, "gbs": vo * 12 / (k_ms / 1e3) / 1e9}
     return {"ms": ms, "value": vo / (ms / 1e3), "unit": UNIT,
-            "what": "forward + loss (torch elementwise) + adjoint, batch 8",
+            "what": "score_energy: forward + weighted energy kernel + weighted adjoint "
+                    "(gradient 2 g w U folded into the plane pass), batch 8",
+            "energy_then_adjoint_ms": ms_energy,
+            "energy_then_adjoint_what": "orientation_score + weighted_energy: the gradient "
+                                        "2 g w U stored, then os3d_adjoint",
+            "torch_loss_ms": ms_torch, "torch_loss_value": vo / (ms_torch / 1e3),
+            "weighted_energy_kernel": ek,
             "transforms_ms": ms_t, "transforms_value": vo / (ms_t / 1e3)}
 
 
@@ -936,6 +963,21 @@ def run_only_op(args):
     import torch
     from paper_1505_07690_gb300 import build, os3d, synth
     build.build()
+    if args.only_op == "autograd":
+        def timed(fn, n):
+            for _ in range(max(args.warmup, 1)):
+                fn()
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            for _ in range(n):
+                fn()
+            b.record()
+            torch.cuda.synchronize()
+            return a.elapsed_time(b) / n
+        r = _autograd_step(os3d, synth, 2 * args.steps, timed)
+        print(json.dumps({"op": "autograd", "workload": "splines96x8_no42", **r}), flush=True)
+        return 0
     w = synth.WORKLOADS[WORKLOAD]
     dims = w["shape"]
     V = os3d.os3d_icosa_orientations(w["subdiv"])

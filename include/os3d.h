@@ -155,6 +155,18 @@ os3d_status os3d_inverse(const os3d_bank* bank, const void* U, os3d_udtype udtyp
 os3d_status os3d_adjoint(const os3d_bank* bank, const void* G, os3d_udtype udtype, int batch,
                          float* grad_f, void* workspace, void* stream);
 
+/* Weighted adjoint: grad_f = Re W^*(2 g w U), the gradient with respect to a
+ * real image f of g sum w |U|^2 at U = W f (os3d_weighted_energy), i.e.
+ * os3d_adjoint of os3d_weighted_energy_grad's G without G being stored: the
+ * plane pass multiplies each element of U by 2 g w as it loads it. U (device,
+ * batch complex64 scores), w (device float, one weight per complex element,
+ * U's layout, 16-byte aligned), g (device float scalar). Errors: EINVAL,
+ * EUNSUPPORTED (BF16 U, or a plane the plane pass does not hold: there
+ * os3d_weighted_energy_grad and os3d_adjoint give the same result), ECUDA. */
+os3d_status os3d_adjoint_weighted(const os3d_bank* bank, const void* U, const float* w,
+                                  const float* g, os3d_udtype udtype, int batch, float* grad_f,
+                                  void* workspace, void* stream);
+
 /* Approximate reconstruction (Eq. Reconstruction2Approximation):
  * f_out = w Re sum_i U_i with the discrete measure w = 1 / (N_o c_0), the
  * value that makes the orientation sum of the wavelets exactly 1 at w = 0
@@ -182,6 +194,33 @@ os3d_status os3d_project(const os3d_bank* bank, const void* U, os3d_udtype udtyp
  * Errors: EINVAL (count, alignment, p <= 0 or not finite), ECUDA. */
 os3d_status os3d_soft_threshold(const void* in, void* out, os3d_udtype udtype, long long count,
                                 double power, void* stream);
+
+/* Weighted energy of a score, L = sum_e w_e |U_e|^2 over `count` complex
+ * elements (a multiple of 4): the squared L_2(R^3 x S^2) norm of the score in
+ * the norm-preservation identity of Sec. 2 (M_psi = 1 gives ||f||^2 =
+ * ||W f||^2), with real weights w (device float, one per complex element,
+ * same layout as U) or w = NULL for w = 1; the loss whose gradient feeds
+ * os3d_adjoint when the transform is differentiated. U, w 16-byte aligned.
+ * `scratch` (device, OS3D_ENERGY_SCRATCH_DOUBLES doubles, 8-byte aligned, not
+ * shared with a concurrent call): scratch[0] receives L in double precision;
+ * if `loss` (device float) is not NULL it receives L rounded to float. Terms
+ * are summed in FP32 over 16 elements and in FP64 above, on a grid fixed by the
+ * device's SM count, with no atomics: the result is bit-identical from call to
+ * call on one device. count = 0 writes L = 0 (U and w may then be NULL).
+ * Errors: EINVAL (count, alignment, NULL scratch, NULL U with count > 0),
+ * ECUDA. */
+#define OS3D_ENERGY_SCRATCH_DOUBLES 4097
+os3d_status os3d_weighted_energy(const void* U, const float* w, os3d_udtype udtype,
+                                 long long count, double* scratch, float* loss, void* stream);
+
+/* Gradient of the weighted energy in PyTorch's convention for complex inputs
+ * (dL/dconj(U) x 2): G = 2 g w U, with the upstream scalar g read from the
+ * device (float, e.g. the incoming gradient of the loss) and w as above (NULL
+ * for 1). G (device, udtype of U, 16-byte aligned) may be U. BF16 results round
+ * to nearest even. count = 0 does nothing. Errors: EINVAL (count, alignment,
+ * NULL pointers with count > 0), ECUDA. */
+os3d_status os3d_weighted_energy_grad(const void* U, const float* w, os3d_udtype udtype,
+                                      long long count, const float* g, void* G, void* stream);
 
 /* Score-domain processing with soft thresholding (Sec. 4.1):
  * Upsilon f = W^{*,ext} Phi W f = W^* P_psi Phi W f, the exact (clamped)
@@ -375,7 +414,9 @@ enum {
   OS3D_KIND_APPROX = 9,        /* approximate reconstruction: orientation sum  */
   OS3D_KIND_SOFT = 10,         /* soft threshold of a stored score             */
   OS3D_KIND_ENHANCE = 11,      /* linear diffusion: per-frequency integration  */
-  OS3D_KIND_COUNT = 12
+  OS3D_KIND_ENERGY = 12,       /* weighted energy: partial sums and final sum  */
+  OS3D_KIND_ENERGY_GRAD = 13,  /* weighted energy: gradient 2 g w U            */
+  OS3D_KIND_COUNT = 14
 };
 
 /* Self-test of the bounded waits (diagnostic): one CTA of 64 threads waits on

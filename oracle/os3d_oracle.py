@@ -36,7 +36,8 @@ Legendre values, B-spline convolution, exact recovery of polynomial
 profiles by both fits, great-circle Funk quadrature, the spherical-harmonic
 addition theorem, M ~ 1, Parseval, Hermitian/antipodal symmetry, exact
 reconstruction, grid-symmetry equivariance, the adjoint identity and finite
-differences; for the diffusion, harmonic polynomials (the Laplace-Beltrami
+differences; for the weighted energy, Parseval with M, a brute-force loop sum
+and central differences along complex directions; for the diffusion, harmonic polynomials (the Laplace-Beltrami
 eigenvalues and the angular decay exp(-t D44 l(l+1))), plane waves along and
 across n (D33 and D11 separately), the heat kernel and the splitting order;
 the radial window against the regularised incomplete gamma function and its
@@ -506,6 +507,27 @@ def project(U, bank: Bank):
     to the embedding space with the M_psi inner product) followed by the
     forward transform (App. A, corollary)."""
     return forward(inverse(U, bank), bank)
+
+
+# ---------------------------------------------------------------------------
+# Weighted energy of a score (Sec. 2, the norm-preservation identity)
+# ---------------------------------------------------------------------------
+def weighted_energy(U, w=None):
+    """L = sum_e w_e |U_e|^2: the squared L_2(R^3 x S^2) norm of a score on
+    the grid (Sec. 2, ||W f||^2 in the norm-preservation identity), with real
+    weights w per element (w = 1 when None)."""
+    a = np.abs(np.asarray(U, dtype=np.complex128)) ** 2
+    if w is not None:
+        a = np.asarray(w, dtype=np.float64) * a
+    return float(np.sum(a))
+
+
+def weighted_energy_grad(U, w=None, g=1.0):
+    """g dL/dconj(U) x 2 = 2 g w U: the gradient of weighted_energy in the
+    convention of PyTorch for complex inputs (the one os3d adjoint consumes)."""
+    U = np.asarray(U, dtype=np.complex128)
+    ww = 1.0 if w is None else np.asarray(w, dtype=np.float64)
+    return 2.0 * g * ww * U
 
 
 # ---------------------------------------------------------------------------

@@ -947,8 +947,11 @@ os3d_status finish_real(const os3d_bank* b, const Work& w, int nblocks, const fl
 // orientation pairs alternate between the two side streams (each with its own
 // intermediates and partial sum), so one block's xy-pass overlaps the other's
 // z-pass.
+// wgt, gscale: the weighted adjoint Re W^*(2 g w U) (the plane pass's weighted
+// load; complex64 U on plane-pass grids), else null
 os3d_status backward_impl(const os3d_bank* b, const void* U, int udtype, int batch, float* fout,
-                          void* ws, cudaStream_t s, bool use_m) {
+                          void* ws, cudaStream_t s, bool use_m, const float* wgt = nullptr,
+                          const float* gscale = nullptr) {
   Work w;
   if (const os3d_status e = workspace_for(b, ws, &w)) return e;
   const int nz = b->dims[0], ny = b->dims[1], nx = b->dims[2];
@@ -965,8 +968,11 @@ os3d_status backward_impl(const os3d_bank* b, const void* U, int udtype, int bat
       set_slots(b, xa, v, s0, ns);
       xa.in = U;
       xa.out = w.T[k];
+      xa.wgt = wgt;
+      xa.gscale = gscale;
+      const int mode = wgt ? XY_INV_WSCORE : XY_INV_SCORE;
       OS3D_CK(counted_launch(OS3D_KIND_XY_INV_SCORE, st,
-                             [&] { return launch_plane(b, XY_INV_SCORE, udtype, xa, st); }));
+                             [&] { return launch_plane(b, mode, udtype, xa, st); }));
       PassArgs za = xa;
       za.in = w.T[k];
       za.out = w.A[k];
@@ -1149,6 +1155,17 @@ os3d_status os3d_adjoint(const os3d_bank* b, const void* G, os3d_udtype udtype, 
   return backward_impl(b, G, udtype, batch, grad_f, ws, (cudaStream_t)stream, false);
 }
 
+os3d_status os3d_adjoint_weighted(const os3d_bank* b, const void* U, const float* w,
+                                  const float* g, os3d_udtype udtype, int batch, float* grad_f,
+                                  void* ws, void* stream) {
+  const os3d_status st = check_call(b, U, grad_f, batch, udtype, ws);
+  if (st != OS3D_OK) return st;
+  if (!w || !g || (reinterpret_cast<uintptr_t>(w) & 15) || (reinterpret_cast<uintptr_t>(g) & 3))
+    return OS3D_EINVAL;
+  if (udtype != OS3D_U_C64 || !xy_supported(b->dims[1], b->dims[2])) return OS3D_EUNSUPPORTED;
+  return backward_impl(b, U, udtype, batch, grad_f, ws, (cudaStream_t)stream, false, w, g);
+}
+
 os3d_status os3d_approx_reconstruct(const os3d_bank* b, const void* U, os3d_udtype udtype,
                                     int batch, float* f_out, void* stream) {
   const os3d_status st = check_call(b, U, f_out, batch, udtype, nullptr);
@@ -1197,6 +1214,37 @@ os3d_status os3d_soft_threshold(const void* in, void* out, os3d_udtype udtype, l
   cudaStream_t s = (cudaStream_t)stream;
   OS3D_CK(counted_launch(OS3D_KIND_SOFT, s, [&] {
     return launch_soft_scores(in, out, udtype == OS3D_U_BF16X2, count, (float)power, s);
+  }));
+  return OS3D_OK;
+}
+
+os3d_status os3d_weighted_energy(const void* U, const float* w, os3d_udtype udtype,
+                                 long long count, double* scratch, float* loss, void* stream) {
+  if (!scratch || count < 0 || count % 4 != 0 || (count > 0 && !U)) return OS3D_EINVAL;
+  if (udtype != OS3D_U_C64 && udtype != OS3D_U_BF16X2) return OS3D_EINVAL;
+  if (((reinterpret_cast<uintptr_t>(U) | reinterpret_cast<uintptr_t>(w)) & 15) ||
+      (reinterpret_cast<uintptr_t>(scratch) & 7) || (reinterpret_cast<uintptr_t>(loss) & 3))
+    return OS3D_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  // an empty score still gets its (zero) sum written
+  OS3D_CK(counted_launch(OS3D_KIND_ENERGY, s, [&] {
+    return launch_energy(U, w, udtype == OS3D_U_BF16X2, count, scratch, loss, s);
+  }));
+  g_launches.fetch_add(1);   // counted_launch counts one of the two
+  return OS3D_OK;
+}
+
+os3d_status os3d_weighted_energy_grad(const void* U, const float* w, os3d_udtype udtype,
+                                      long long count, const float* g, void* G, void* stream) {
+  if (count < 0 || count % 4 != 0 || (count > 0 && (!U || !g || !G))) return OS3D_EINVAL;
+  if (udtype != OS3D_U_C64 && udtype != OS3D_U_BF16X2) return OS3D_EINVAL;
+  if (((reinterpret_cast<uintptr_t>(U) | reinterpret_cast<uintptr_t>(w) |
+        reinterpret_cast<uintptr_t>(G)) & 15) || (reinterpret_cast<uintptr_t>(g) & 3))
+    return OS3D_EINVAL;
+  if (count == 0) return OS3D_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  OS3D_CK(counted_launch(OS3D_KIND_ENERGY_GRAD, s, [&] {
+    return launch_energy_grad(U, w, udtype == OS3D_U_BF16X2, count, g, G, s);
   }));
   return OS3D_OK;
 }
@@ -1481,7 +1529,8 @@ os3d_status os3d_profile_reset(void) {
 const char* os3d_kernel_kind_name(int kind) {
   static const char* names[OS3D_KIND_COUNT] = {
       "xy_fwd_real", "xy_fwd_score", "xy_inv_score", "xy_inv_real", "z_fwd_prep", "z_fwd_score",
-      "z_inv_score", "z_inv_final", "xy_soft", "approx_sum", "soft_threshold", "enhance_linear"};
+      "z_inv_score", "z_inv_final", "xy_soft", "approx_sum", "soft_threshold", "enhance_linear",
+      "weighted_energy", "weighted_energy_grad"};
   return (kind >= 0 && kind < OS3D_KIND_COUNT) ? names[kind] : "unknown";
 }
 

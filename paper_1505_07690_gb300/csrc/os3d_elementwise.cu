@@ -1,8 +1,9 @@
 // Streaming kernels of the score domain (sm_103a): the orientation sum of the
-// approximate reconstruction (Eq. Reconstruction2Approximation) and the soft
+// approximate reconstruction (Eq. Reconstruction2Approximation), the soft
 // threshold Phi(U) = |U|^p sgn(U) of Sec. 4.1, on whole scores and on the
-// per-block intermediates. All are HBM-bound: 16-byte vector loads and
-// stores, one pass over their data.
+// per-block intermediates, and the weighted energy sum w |U|^2 (the squared
+// L_2(R^3 x S^2) norm of Sec. 2) with its gradient. All are HBM-bound:
+// 16-byte vector loads and stores, one pass over their data.
 #include <cuda_bf16.h>
 #include <algorithm>
 #include "os3d_kernels.cuh"
@@ -93,10 +94,148 @@ soft_slots_kernel(const __grid_constant__ PassArgs a, long long nvox) {
                      scale * soft_part(v.z, a.power), scale * soft_part(v.w, a.power));
 }
 
-int grid_for(long long items) {
+// Weighted energy. A thread takes quads of 4 complex elements (one 16-byte
+// weight vector, 16 or 32 bytes of score) kEChunk grid strides apart, sums
+// those 16 terms in FP32 and adds the chunk to an FP64 accumulator; blocks
+// reduce in FP64 in a fixed order. Nothing depends on timing, so a call is
+// bit-identical to the last on the same grid.
+constexpr int kEChunk = 4;
+
+template <int UBF16, int WEIGHTED>
+__device__ __forceinline__ float quad_energy(const void* __restrict__ U,
+                                             const float* __restrict__ w, long long q) {
+  float4 c = make_float4(1.f, 1.f, 1.f, 1.f);
+  if constexpr (WEIGHTED) c = __ldcs(reinterpret_cast<const float4*>(w) + q);
+  float e0, e1, e2, e3;
+  if constexpr (UBF16) {
+    const uint4 v = __ldcs(reinterpret_cast<const uint4*>(U) + q);
+    const float r0 = bf16_lo(v.x), i0 = __uint_as_float(v.x & 0xffff0000u);
+    const float r1 = bf16_lo(v.y), i1 = __uint_as_float(v.y & 0xffff0000u);
+    const float r2 = bf16_lo(v.z), i2 = __uint_as_float(v.z & 0xffff0000u);
+    const float r3 = bf16_lo(v.w), i3 = __uint_as_float(v.w & 0xffff0000u);
+    e0 = r0 * r0 + i0 * i0;
+    e1 = r1 * r1 + i1 * i1;
+    e2 = r2 * r2 + i2 * i2;
+    e3 = r3 * r3 + i3 * i3;
+  } else {
+    const float4 a = __ldcs(reinterpret_cast<const float4*>(U) + 2 * q);
+    const float4 b = __ldcs(reinterpret_cast<const float4*>(U) + 2 * q + 1);
+    e0 = a.x * a.x + a.y * a.y;
+    e1 = a.z * a.z + a.w * a.w;
+    e2 = b.x * b.x + b.y * b.y;
+    e3 = b.z * b.z + b.w * b.w;
+  }
+  return (c.x * e0 + c.y * e1) + (c.z * e2 + c.w * e3);
+}
+
+// FP64 sum over the block, fixed order (warp shuffles, then the warp sums in
+// index order); the result is valid in thread 0.
+__device__ __forceinline__ double block_sum(double a) {
+  __shared__ double warp_sums[kThreads / 32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+  if ((threadIdx.x & 31) == 0) warp_sums[threadIdx.x >> 5] = a;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0)
+    for (int i = 0; i < kThreads / 32; ++i) t += warp_sums[i];
+  return t;
+}
+
+template <int UBF16, int WEIGHTED>
+__global__ void __launch_bounds__(kThreads)
+energy_partial_kernel(const void* __restrict__ U, const float* __restrict__ w, long long nq,
+                      double* __restrict__ partial) {
+  const long long stride = (long long)gridDim.x * kThreads;
+  double acc = 0.0;
+  for (long long q0 = (long long)blockIdx.x * kThreads + threadIdx.x; q0 < nq;
+       q0 += kEChunk * stride) {
+    float s = 0.f;
+#pragma unroll
+    for (int j = 0; j < kEChunk; ++j) {
+      const long long q = q0 + j * stride;
+      if (q < nq) s += quad_energy<UBF16, WEIGHTED>(U, w, q);
+    }
+    acc += (double)s;
+  }
+  const double t = block_sum(acc);
+  if (threadIdx.x == 0) partial[blockIdx.x] = t;
+}
+
+__global__ void __launch_bounds__(kThreads)
+energy_final_kernel(double* __restrict__ scratch, int nblocks, float* __restrict__ loss) {
+  double a = 0.0;
+  for (int i = threadIdx.x; i < nblocks; i += kThreads) a += scratch[1 + i];
+  const double t = block_sum(a);
+  if (threadIdx.x == 0) {
+    scratch[0] = t;
+    if (loss) *loss = (float)t;
+  }
+}
+
+// G = 2 g w U per quad (G may be U).
+template <int UBF16, int WEIGHTED>
+__global__ void __launch_bounds__(kThreads)
+energy_grad_kernel(const void* U, const float* __restrict__ w, const float* __restrict__ g,
+                   long long nq, void* G) {
+  const float c2 = 2.f * __ldg(g);
+  const long long stride = (long long)gridDim.x * kThreads;
+  for (long long q = (long long)blockIdx.x * kThreads + threadIdx.x; q < nq; q += stride) {
+    float4 c = make_float4(c2, c2, c2, c2);
+    if constexpr (WEIGHTED) {
+      const float4 wq = __ldcs(reinterpret_cast<const float4*>(w) + q);
+      c = make_float4(c2 * wq.x, c2 * wq.y, c2 * wq.z, c2 * wq.w);
+    }
+    if constexpr (UBF16) {
+      uint4 v = __ldcs(reinterpret_cast<const uint4*>(U) + q);
+      unsigned* e = reinterpret_cast<unsigned*>(&v);
+      const float cj[4] = {c.x, c.y, c.z, c.w};
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&e[j]));
+        __nv_bfloat162 b = __floats2bfloat162_rn(cj[j] * f.x, cj[j] * f.y);
+        e[j] = *reinterpret_cast<unsigned*>(&b);
+      }
+      __stcs(reinterpret_cast<uint4*>(G) + q, v);
+    } else {
+      const float4 a = __ldcs(reinterpret_cast<const float4*>(U) + 2 * q);
+      const float4 b = __ldcs(reinterpret_cast<const float4*>(U) + 2 * q + 1);
+      __stcs(reinterpret_cast<float4*>(G) + 2 * q,
+             make_float4(c.x * a.x, c.x * a.y, c.y * a.z, c.y * a.w));
+      __stcs(reinterpret_cast<float4*>(G) + 2 * q + 1,
+             make_float4(c.z * b.x, c.z * b.y, c.w * b.z, c.w * b.w));
+    }
+  }
+}
+
+int sm_count() {
   int dev = 0, nsm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  return nsm;
+}
+
+template <int UBF16, int WEIGHTED>
+cudaError_t launch_energy_t(const void* U, const float* w, long long nq, double* scratch,
+                            float* loss, cudaStream_t s) {
+  // every SM full once: blocks resident per SM x SM count, capped by the
+  // scratch and by the work
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+      &per_sm, energy_partial_kernel<UBF16, WEIGHTED>, kThreads, 0);
+  if (e != cudaSuccess) return e;
+  const long long need = (nq + kThreads - 1) / kThreads;
+  const int grid = (int)std::max(1LL, std::min({(long long)std::max(per_sm, 1) * sm_count(), need,
+                                                (long long)kMaxEnergyBlocks}));
+  energy_partial_kernel<UBF16, WEIGHTED><<<grid, kThreads, 0, s>>>(U, w, nq, scratch + 1);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  energy_final_kernel<<<1, kThreads, 0, s>>>(scratch, grid, loss);
+  return cudaGetLastError();
+}
+
+int grid_for(long long items) {
+  const int nsm = sm_count();
   const long long need = (items + kThreads - 1) / kThreads;
   return (int)std::max(1LL, std::min(need, (long long)nsm * 16));
 }
@@ -122,6 +261,29 @@ cudaError_t launch_soft_scores(const void* in, void* out, int ubf16, long long c
 cudaError_t launch_soft_slots(const PassArgs& a, long long nvox, cudaStream_t s) {
   const dim3 grid((unsigned)((nvox / 2 + kThreads - 1) / kThreads), (unsigned)a.nslots);
   soft_slots_kernel<<<grid, kThreads, 0, s>>>(a, nvox);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_energy(const void* U, const float* w, int ubf16, long long count,
+                          double* scratch, float* loss, cudaStream_t s) {
+  const long long nq = count / 4;
+  if (ubf16) return w ? launch_energy_t<1, 1>(U, w, nq, scratch, loss, s)
+                      : launch_energy_t<1, 0>(U, w, nq, scratch, loss, s);
+  return w ? launch_energy_t<0, 1>(U, w, nq, scratch, loss, s)
+           : launch_energy_t<0, 0>(U, w, nq, scratch, loss, s);
+}
+
+cudaError_t launch_energy_grad(const void* U, const float* w, int ubf16, long long count,
+                               const float* g, void* G, cudaStream_t s) {
+  const long long nq = count / 4;
+  const int grid = grid_for(nq);
+  if (ubf16) {
+    if (w) energy_grad_kernel<1, 1><<<grid, kThreads, 0, s>>>(U, w, g, nq, G);
+    else energy_grad_kernel<1, 0><<<grid, kThreads, 0, s>>>(U, w, g, nq, G);
+  } else {
+    if (w) energy_grad_kernel<0, 1><<<grid, kThreads, 0, s>>>(U, w, g, nq, G);
+    else energy_grad_kernel<0, 0><<<grid, kThreads, 0, s>>>(U, w, g, nq, G);
+  }
   return cudaGetLastError();
 }
 

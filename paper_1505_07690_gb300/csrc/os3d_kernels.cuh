@@ -36,7 +36,10 @@ enum ZMode { Z_FWD_PREP = 0, Z_FWD_SCORE = 1, Z_INV_SCORE = 2, Z_INV_FINAL = 3 }
 //  XY_INV_REAL : T0 -> IDFT_xy -> real part                        -> f
 //  XY_SOFT     : T_s -> IDFT_xy -> m_s Phi(.) -> DFT_xy             -> T_s (in place)
 //                (Phi the soft threshold |u|^p sgn(u) per part, m_s = 2 for a pair)
-enum XYMode { XY_FWD_REAL = 0, XY_FWD_SCORE = 1, XY_INV_SCORE = 2, XY_INV_REAL = 3, XY_SOFT = 4 };
+// XY_INV_WSCORE: XY_INV_SCORE on the weighted input 2 g (w_a U_a + conj(w_b U_b))
+// (the gradient of g sum w |U|^2, folded into the load; complex64 U)
+enum XYMode { XY_FWD_REAL = 0, XY_FWD_SCORE = 1, XY_INV_SCORE = 2, XY_INV_REAL = 3, XY_SOFT = 4,
+              XY_INV_WSCORE = 5 };
 
 struct PassArgs {
   const void* in;
@@ -57,6 +60,8 @@ struct PassArgs {
                               // skipped by the z-passes and read as zero / not written
                               // by the plane passes (cluster plane path only)
   float nvec[kMaxSlots][3];   // orientation n_a (x, y, z) of each slot
+  const float* wgt;           // XY_INV_WSCORE: weight per element, U's layout
+  const float* gscale;        // XY_INV_WSCORE: the scalar g (device)
   HEval h;
 };
 
@@ -99,6 +104,14 @@ cudaError_t launch_approx_sum(const void* U, int ubf16, int n_o, long long nvox,
                               float* out, cudaStream_t s);
 cudaError_t launch_soft_scores(const void* in, void* out, int ubf16, long long count,
                                float power, cudaStream_t s);
+// weighted energy L = sum w |U|^2 (os3d_elementwise.cu): block partial sums
+// into scratch[1 ..], their sum into scratch[0] and *loss (when not null);
+// the gradient G = 2 g w U with g read on the device. w may be null (w = 1).
+constexpr int kMaxEnergyBlocks = 4096;
+cudaError_t launch_energy(const void* U, const float* w, int ubf16, long long count,
+                          double* scratch, float* loss, cudaStream_t s);
+cudaError_t launch_energy_grad(const void* U, const float* w, int ubf16, long long count,
+                               const float* g, void* G, cudaStream_t s);
 // in place on a.nslots volumes of a.out, a.slot_stride apart, nvox each;
 // slot s scaled by 2 when a.ub[s] >= 0 (an antipodal pair)
 cudaError_t launch_soft_slots(const PassArgs& a, long long nvox, cudaStream_t s);

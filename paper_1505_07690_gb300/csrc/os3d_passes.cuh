@@ -420,7 +420,9 @@ xy_kernel(const __grid_constant__ PassArgs a) {
   constexpr int NS = XYSplit<NY, NX>::NS;
   constexpr int R1x = C::R1x, R2x = C::R2x, R1y = C::R1y, R2y = C::R2y;
   constexpr int NT = C::NT, NYH = C::NYH, NXH = C::NXH;
-  constexpr int DIR = (MODE == XY_FWD_REAL || MODE == XY_INV_SCORE) ? -1 : +1;
+  constexpr bool INV = MODE == XY_INV_SCORE || MODE == XY_INV_WSCORE;   // score -> T
+  constexpr int DIR = (MODE == XY_FWD_REAL || INV) ? -1 : +1;
+  static_assert(MODE != XY_INV_WSCORE || !UBF16, "the weighted load takes complex64 scores");
 
   extern __shared__ __align__(16) float2 sm[];
   float2* work = sm;
@@ -434,7 +436,9 @@ xy_kernel(const __grid_constant__ PassArgs a) {
   for (int q = 0; q < NS; ++q) peer_base[q] = map_cluster_rank(smem_addr(work), (unsigned)q);
   const long long P = (long long)NY * NX;
   const int cl = blockIdx.x / NS, ncl = gridDim.x / NS;
-  const int nsl = (MODE == XY_FWD_SCORE || MODE == XY_INV_SCORE) ? a.nslots : 1;
+  const int nsl = (MODE == XY_FWD_SCORE || INV) ? a.nslots : 1;
+  float c2 = 0.f;   // 2 g of the weighted load
+  if constexpr (MODE == XY_INV_WSCORE) c2 = 2.f * __ldg(a.gscale);
   const int nunits = a.nz * nsl;
 
   fill_twiddles<NX, DIR>(twx);
@@ -447,7 +451,7 @@ xy_kernel(const __grid_constant__ PassArgs a) {
     // ---- x direction, step 1 on this CTA's rows (global -> registers -> shared)
     {
       long long ia, ib = -1;
-      if constexpr (MODE == XY_INV_SCORE) {
+      if constexpr (INV) {
         ia = a.ua[s];
         ib = a.ub[s];
       } else if constexpr (MODE == XY_FWD_SCORE) {
@@ -473,6 +477,10 @@ xy_kernel(const __grid_constant__ PassArgs a) {
             float2 q = load_u<UBF16>(a.in, ia + e);
             if (ib >= 0) q = cadd(q, cconj(load_u<UBF16>(a.in, ib + e)));
             v[n1] = q;
+          } else if constexpr (MODE == XY_INV_WSCORE) {
+            float2 q = cscale(load_u<0>(a.in, ia + e), __ldcs(a.wgt + ia + e));
+            if (ib >= 0) q = cadd(q, cconj(cscale(load_u<0>(a.in, ib + e), __ldcs(a.wgt + ib + e))));
+            v[n1] = cscale(q, c2);
           } else if constexpr (MODE == XY_FWD_SCORE) {
             v[n1] = (a.disc && tile_outside(n2 + R2x * n1, h * NYH + r, NX, NY))
                         ? make_float2(0.f, 0.f)
@@ -489,10 +497,10 @@ xy_kernel(const __grid_constant__ PassArgs a) {
     }
     __syncthreads();
     // the input rows of this CTA's next unit go to L2 while this one runs
-    if (t == 0 && (MODE == XY_FWD_SCORE || MODE == XY_INV_SCORE) && u + ncl < nunits) {
+    if (t == 0 && (MODE == XY_FWD_SCORE || INV) && u + ncl < nunits) {
       const int zn = (u + ncl) % a.nz, sn = (u + ncl) / a.nz;
       const long long rows = (long long)zn * P + (long long)h * NYH * NX;
-      constexpr unsigned esz = (MODE == XY_INV_SCORE && UBF16) ? 4u : 8u;
+      constexpr unsigned esz = (INV && UBF16) ? 4u : 8u;
       constexpr unsigned bytes = (unsigned)(NYH * NX) * esz;
       const char* base = reinterpret_cast<const char*>(a.in);
       if constexpr (MODE == XY_FWD_SCORE) {
@@ -500,6 +508,10 @@ xy_kernel(const __grid_constant__ PassArgs a) {
       } else {
         prefetch_l2(base + esz * (a.ua[sn] + rows), bytes);
         if (a.ub[sn] >= 0) prefetch_l2(base + esz * (a.ub[sn] + rows), bytes);
+        if constexpr (MODE == XY_INV_WSCORE) {
+          prefetch_l2(a.wgt + a.ua[sn] + rows, bytes / 2);
+          if (a.ub[sn] >= 0) prefetch_l2(a.wgt + a.ub[sn] + rows, bytes / 2);
+        }
       }
     }
     // ---- x direction, step 2; outputs go to the owner of their column
@@ -558,7 +570,7 @@ xy_kernel(const __grid_constant__ PassArgs a) {
       if constexpr (MODE == XY_FWD_SCORE) {
         o = a.ua[s];
         ob = a.ub[s];
-      } else if constexpr (MODE == XY_INV_SCORE) {
+      } else if constexpr (INV) {
         o = (long long)s * a.slot_stride;
       } else {
         o = a.out_off;
@@ -580,7 +592,7 @@ xy_kernel(const __grid_constant__ PassArgs a) {
             if (ob >= 0) store_u<UBF16>(a.out, ob + e, cconj(w[k2]));
           } else if constexpr (MODE == XY_INV_REAL) {
             reinterpret_cast<float*>(a.out)[o + e] = w[k2].x;
-          } else if constexpr (MODE == XY_INV_SCORE) {
+          } else if constexpr (INV) {
             if (!(a.disc && tile_outside(h * NXH + c, k1 + R1y * k2, NX, NY)))
               reinterpret_cast<float2*>(a.out)[o + e] = w[k2];
           } else {
@@ -874,7 +886,8 @@ cudaError_t launch_xy_one(const PassArgs& a, cudaStream_t s) {
   int dev = 0, nsm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  const int nsl = (MODE == XY_FWD_SCORE || MODE == XY_INV_SCORE) ? a.nslots : 1;
+  const int nsl = (MODE == XY_FWD_SCORE || MODE == XY_INV_SCORE || MODE == XY_INV_WSCORE)
+                      ? a.nslots : 1;
   // two CTAs per SM, NS per cluster, looping over units; a whole plane per CTA:
   // as many CTAs as are resident at once
   constexpr int NS = XYSplit<NY, NX>::NS;
@@ -900,6 +913,9 @@ cudaError_t launch_xy_n(int mode, int ub, const PassArgs& a, cudaStream_t s) {
     case XY_INV_SCORE:
       return ub ? launch_xy_one<NY, NX, XY_INV_SCORE, 1>(a, s)
                 : launch_xy_one<NY, NX, XY_INV_SCORE, 0>(a, s);
+    case XY_INV_WSCORE:
+      if (ub) return cudaErrorInvalidValue;
+      return launch_xy_one<NY, NX, XY_INV_WSCORE, 0>(a, s);
     case XY_SOFT:
       if constexpr (NX <= 128) return launch_xy_soft_one<NY, NX>(a, s);
       else return cudaErrorInvalidValue;

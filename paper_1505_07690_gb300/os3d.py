@@ -19,6 +19,7 @@ OS3D_U_C64 = 0
 OS3D_U_BF16X2 = 1
 _STATUS = {0: "OS3D_OK", 1: "OS3D_EINVAL", 2: "OS3D_ENOMEM", 3: "OS3D_ECUDA",
            4: "OS3D_ETIMEOUT", 5: "OS3D_EUNSUPPORTED"}
+OS3D_EUNSUPPORTED = 5
 
 
 class os3d_params(ctypes.Structure):
@@ -65,6 +66,8 @@ def lib():
         L.os3d_approx_reconstruct.argtypes = [vp, vp, i, i, vp, vp]
         L.os3d_project.argtypes = [vp, vp, i, i, vp, vp, vp]
         L.os3d_soft_threshold.argtypes = [vp, vp, i, ctypes.c_longlong, d, vp]
+        L.os3d_weighted_energy.argtypes = [vp, vp, i, ctypes.c_longlong, vp, vp, vp]
+        L.os3d_weighted_energy_grad.argtypes = [vp, vp, i, ctypes.c_longlong, vp, vp, vp]
         L.os3d_upsilon.argtypes = [vp, vp, i, vp, d, vp, vp]
         L.os3d_default_diffusion.argtypes = [ctypes.POINTER(os3d_diffusion)]
         L.os3d_angular_propagator.argtypes = [ctypes.POINTER(d), i, i, d, ctypes.POINTER(d),
@@ -75,6 +78,7 @@ def lib():
         L.os3d_forward.argtypes = [vp, vp, i, vp, i, vp, vp]
         L.os3d_inverse.argtypes = [vp, vp, i, i, vp, vp, vp]
         L.os3d_adjoint.argtypes = [vp, vp, i, i, vp, vp, vp]
+        L.os3d_adjoint_weighted.argtypes = [vp, vp, vp, vp, i, i, vp, vp, vp]
         L.os3d_bank_info.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t),
                                      ctypes.POINTER(ctypes.c_size_t)]
         L.os3d_bank_resident_bytes.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t)]
@@ -111,7 +115,9 @@ def lib():
                      "os3d_approx_reconstruct", "os3d_project", "os3d_soft_threshold",
                      "os3d_upsilon", "os3d_default_diffusion", "os3d_enhance_linear",
                      "os3d_angular_propagator", "os3d_server_stats",
-                     "os3d_bank_resident_bytes", "os3d_bank_wait_errors", "os3d_wait_selftest"):
+                     "os3d_bank_resident_bytes", "os3d_bank_wait_errors", "os3d_wait_selftest",
+                     "os3d_weighted_energy", "os3d_weighted_energy_grad",
+                     "os3d_adjoint_weighted"):
             getattr(L, name).restype = i
         _lib = L
     return _lib
@@ -325,6 +331,25 @@ def os3d_adjoint(bank: Bank, G, grad_f=None, workspace=None, stream=None):
     return _backward(lib().os3d_adjoint, "os3d_adjoint", bank, G, grad_f, workspace, stream)
 
 
+def os3d_adjoint_weighted(bank: Bank, U, w, g=None, grad_f=None, workspace=None, stream=None):
+    """Re W^*(2 g w U), the gradient of g sum w |U|^2 at U = W f, with the
+    weighting folded into the plane pass (complex64 U; OS3DError with
+    OS3D_EUNSUPPORTED where the plane pass does not hold the grid's planes)."""
+    import torch
+    if g is None:
+        g = torch.ones((), dtype=torch.float32, device="cuda")
+    if not (g.is_cuda and g.dtype == torch.float32 and g.numel() == 1):
+        raise ValueError("g must be a one-element float32 CUDA tensor")
+    _, count, wp = _energy_operands(U, w)
+    if w is None:
+        raise ValueError("w is required (w = 1 is os3d_adjoint of 2 g U)")
+    gc = g.contiguous()
+
+    def fn(h, Up, ud, batch, out, ws, st):
+        return lib().os3d_adjoint_weighted(h, Up, wp, _ptr(gc), ud, batch, out, ws, st)
+    return _backward(fn, "os3d_adjoint_weighted", bank, U, grad_f, workspace, stream)
+
+
 def os3d_approx_reconstruct(bank: Bank, U, f_out=None, stream=None):
     """Approximate reconstruction Re sum_i U_i / (N_o c_0)
     (Eq. Reconstruction2Approximation)."""
@@ -367,6 +392,58 @@ def os3d_soft_threshold(U, power: float = 1.5, out=None, stream=None):
     count = U.numel() // 2 if ud == OS3D_U_BF16X2 else U.numel()
     _check(lib().os3d_soft_threshold(_ptr(U), _ptr(out), ud, count, float(power), _stream(stream)),
            "os3d_soft_threshold")
+    return out
+
+
+OS3D_ENERGY_SCRATCH_DOUBLES = 4097
+
+
+def _energy_operands(U, w):
+    import torch
+    ud = _udtype(U)
+    if not (U.is_cuda and U.is_contiguous()):
+        raise ValueError("U must be a contiguous CUDA tensor")
+    count = U.numel() // 2 if ud == OS3D_U_BF16X2 else U.numel()
+    if w is not None:
+        if not (w.is_cuda and w.dtype == torch.float32 and w.is_contiguous()
+                and w.numel() == count):
+            raise ValueError("w must be a contiguous float32 CUDA tensor, one weight per "
+                             "complex element of U")
+    return ud, count, (ctypes.c_void_p(None) if w is None else _ptr(w))
+
+
+def os3d_weighted_energy(U, w=None, scratch=None, stream=None):
+    """L = sum w |U|^2 (w = 1 when None) as a 0-dim float32 CUDA tensor, summed
+    in FP32 over 16 terms and FP64 above; `scratch` (float64 CUDA tensor of
+    OS3D_ENERGY_SCRATCH_DOUBLES) keeps the FP64 sum in scratch[0]."""
+    import torch
+    ud, count, wp = _energy_operands(U, w)
+    if scratch is None:
+        scratch = torch.empty(OS3D_ENERGY_SCRATCH_DOUBLES, dtype=torch.float64, device=U.device)
+    if not (scratch.is_cuda and scratch.dtype == torch.float64 and scratch.is_contiguous()
+            and scratch.numel() >= OS3D_ENERGY_SCRATCH_DOUBLES):
+        raise ValueError("scratch must be a float64 CUDA tensor of OS3D_ENERGY_SCRATCH_DOUBLES")
+    loss = torch.empty((), dtype=torch.float32, device=U.device)
+    _check(lib().os3d_weighted_energy(_ptr(U), wp, ud, count, _ptr(scratch), _ptr(loss),
+                                      _stream(stream)), "os3d_weighted_energy")
+    return loss
+
+
+def os3d_weighted_energy_grad(U, w=None, g=None, out=None, stream=None):
+    """G = 2 g w U (PyTorch's gradient of sum w |U|^2 scaled by the upstream
+    0-dim float32 CUDA tensor g, 1 when None); out may be U."""
+    import torch
+    ud, count, wp = _energy_operands(U, w)
+    if g is None:
+        g = torch.ones((), dtype=torch.float32, device=U.device)
+    if not (g.is_cuda and g.dtype == torch.float32 and g.numel() == 1):
+        raise ValueError("g must be a one-element float32 CUDA tensor")
+    if out is None:
+        out = torch.empty_like(U)
+    if out.dtype != U.dtype or out.shape != U.shape or not out.is_contiguous():
+        raise ValueError("out must match U")
+    _check(lib().os3d_weighted_energy_grad(_ptr(U), wp, ud, count, _ptr(g.contiguous()), _ptr(out),
+                                           _stream(stream)), "os3d_weighted_energy_grad")
     return out
 
 
@@ -427,7 +504,7 @@ def os3d_enhance_linear(bank: Bank, f, diffusion: os3d_diffusion | None = None, 
     return f_out
 
 
-OS3D_KIND_COUNT = 12
+OS3D_KIND_COUNT = 14
 
 
 def os3d_wait_selftest(limit_s: float, arrive: bool) -> int:

@@ -17,14 +17,14 @@ def oracle_map(fn, jobs):
         return pool.map(fn, jobs, chunksize=1)
 
 
-def adjoint_of_weighted_score(job):
-    """Re W^*(2 w W f) of one volume with the oracle (the gradient of
-    sum w |W f|^2): job = (f, w, dims, subdiv, L)."""
-    import numpy as np
+def energy_and_adjoint_of_weighted_score(job):
+    """(sum w |W f|^2, Re W^*(2 w W f)) of one volume with the oracle:
+    job = (f, w, dims, subdiv, L)."""
     from oracle import os3d_oracle as O
     f, w, dims, subdiv, L = job
     ob = O.Bank(dims, O.icosa_orientations(subdiv), O.Params(L=L))
-    return O.adjoint(2.0 * w.astype(np.float64) * O.forward(f, ob), ob)
+    U = O.forward(f, ob)
+    return O.weighted_energy(U, w), O.adjoint(O.weighted_energy_grad(U, w), ob)
 
 
 def upsilon_of(job):

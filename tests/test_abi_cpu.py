@@ -111,6 +111,7 @@ def test_argument_errors_before_any_launch(L):
     assert L.os3d_forward(None, None, 1, None, 0, None, None) == 1
     assert L.os3d_inverse(None, None, 0, 1, None, None, None) == 1
     assert L.os3d_adjoint(None, None, 0, 1, None, None, None) == 1
+    assert L.os3d_adjoint_weighted(None, None, None, None, 0, 1, None, None, None) == 1
     assert L.os3d_bank_info(None, None, None) == 1
     assert L.os3d_destroy_bank(None) == 1
     assert L.os3d_approx_reconstruct(None, None, 0, 1, None, None) == 1
@@ -126,6 +127,21 @@ def test_argument_errors_before_any_launch(L):
         assert L.os3d_soft_threshold(a16, a16, 0, 4, pw, None) == 1
     assert L.os3d_soft_threshold(a16, a16, 2, 4, 1.5, None) == 1       # unknown udtype
     assert L.os3d_soft_threshold(a16, a16, 0, 0, 1.5, None) == 0       # nothing to do
+    # weighted energy and its gradient: count, pointers, alignment, udtype
+    assert L.os3d_weighted_energy(a16, None, 0, 6, a16, None, None) == 1      # count % 4
+    assert L.os3d_weighted_energy(a16, None, 0, -4, a16, None, None) == 1
+    assert L.os3d_weighted_energy(a16, None, 0, 4, None, None, None) == 1     # no scratch
+    assert L.os3d_weighted_energy(None, None, 0, 4, a16, None, None) == 1     # no score
+    assert L.os3d_weighted_energy(a16 + 8, None, 0, 4, a16, None, None) == 1  # misaligned U
+    assert L.os3d_weighted_energy(a16, a16 + 4, 0, 4, a16, None, None) == 1   # misaligned w
+    assert L.os3d_weighted_energy(a16, None, 0, 4, a16 + 4, None, None) == 1  # scratch
+    assert L.os3d_weighted_energy(a16, None, 2, 4, a16, None, None) == 1      # udtype
+    assert L.os3d_weighted_energy_grad(a16, None, 0, 4, None, a16, None) == 1  # no g
+    assert L.os3d_weighted_energy_grad(a16, None, 0, 4, a16, None, None) == 1  # no G
+    assert L.os3d_weighted_energy_grad(a16, None, 0, 4, a16, a16 + 8, None) == 1
+    assert L.os3d_weighted_energy_grad(a16, None, 0, 5, a16, a16, None) == 1
+    assert L.os3d_weighted_energy_grad(a16, None, 2, 4, a16, a16, None) == 1
+    assert L.os3d_weighted_energy_grad(None, None, 0, 0, None, None, None) == 0  # nothing to do
     d = os3d.os3d_default_diffusion()
     assert (d.t, d.steps, d.D11, d.D33, d.D44, d.sh_degree) == (10.0, 8, 0.0, 1.0, 0.01, 0)
     assert L.os3d_enhance_linear(None, None, 1, None, ctypes.byref(d), None, None) == 1

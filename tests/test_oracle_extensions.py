@@ -362,3 +362,70 @@ def test_radial_window_is_the_regularised_upper_gamma_with_its_inflection_at_gam
                     + O.radial_window(r - h, N, gamma)) / h ** 2
     assert d2(r0 - 0.02) < 0.0 < d2(r0 + 0.02)
     assert abs(d2(r0)) < 1e-3 * abs(d2(r0 - 0.3))
+
+
+# ---------------------------------------------------------------------------
+# weighted energy sum w |U|^2 of a score (Sec. 2, norm preservation)
+# ---------------------------------------------------------------------------
+def test_weighted_energy_of_a_score_is_parseval_with_M():
+    # sum_i sum_x |U_i|^2 = (1/n^3) sum_w M(w) |f_hat(w)|^2: with M = 1 this is
+    # the norm preservation ||W f||^2 = ||f||^2 of Sec. 2
+    dims = (12, 10, 16)
+    rng = np.random.default_rng(31)
+    f = rng.standard_normal(dims)
+    bank = O.Bank(dims, O.icosa_orientations(1), O.Params(L=12))
+    U = O.forward(f, bank)
+    rhs = np.sum(bank.M() * np.abs(np.fft.fftn(f)) ** 2) / np.prod(dims)
+    assert abs(O.weighted_energy(U) - rhs) <= 1e-12 * rhs
+    # a plane wave inside the pass band, where M ~ 1: the energy is ||f||^2
+    z, y, x = np.meshgrid(*[np.arange(n) for n in dims], indexing="ij")
+    k = (1, 1, 2)
+    pw = np.cos(2 * np.pi * (k[0] * z / dims[0] + k[1] * y / dims[1] + k[2] * x / dims[2]))
+    e = O.weighted_energy(O.forward(pw, bank))
+    m = bank.M()[k]
+    assert abs(e - m * np.sum(pw ** 2)) <= 1e-12 * e
+    assert abs(m - 1.0) < 0.05
+
+
+def test_weighted_energy_is_the_loop_sum():
+    rng = np.random.default_rng(32)
+    U = rng.standard_normal((3, 2, 4)) + 1j * rng.standard_normal((3, 2, 4))
+    w = rng.uniform(0, 1, U.shape)
+    s = 0.0
+    for idx in np.ndindex(U.shape):
+        s += w[idx] * (U[idx].real ** 2 + U[idx].imag ** 2)
+    assert abs(O.weighted_energy(U, w) - s) <= 1e-14 * s
+    assert O.weighted_energy(np.zeros((0, 4), complex)) == 0.0
+    assert abs(O.weighted_energy(U) - sum(abs(u) ** 2 for u in U.ravel())) <= 1e-13
+
+
+def _energy_grad_mismatch(grad_fn, seed=33):
+    """max relative gap between central differences of L(U + t D) and the
+    directional derivative Re sum conj(G) D that PyTorch's convention assigns
+    to the gradient G (L is quadratic, so the difference quotient is exact up
+    to rounding)."""
+    rng = np.random.default_rng(seed)
+    U = rng.standard_normal((4, 5, 6)) + 1j * rng.standard_normal((4, 5, 6))
+    w = rng.uniform(0, 1, U.shape)
+    g = 0.75
+    worst = 0.0
+    for _ in range(4):
+        D = rng.standard_normal(U.shape) + 1j * rng.standard_normal(U.shape)
+        h = 1e-3
+        fd = g * (O.weighted_energy(U + h * D, w) - O.weighted_energy(U - h * D, w)) / (2 * h)
+        dd = float(np.real(np.vdot(grad_fn(U, w, g), D)))
+        worst = max(worst, abs(fd - dd) / abs(fd))
+    return worst
+
+
+def test_weighted_energy_gradient_by_central_differences():
+    assert _energy_grad_mismatch(O.weighted_energy_grad) < 1e-10
+
+
+def test_energy_gradient_pin_fails_on_planted_mistakes():
+    planted = [lambda U, w, g: g * w * U,                 # factor 2 dropped
+               lambda U, w, g: 2 * g * w * np.conj(U),    # conjugate taken
+               lambda U, w, g: 2 * g * U,                 # weight dropped
+               lambda U, w, g: 2 * w * U]                 # upstream scalar dropped
+    for bad in planted:
+        assert _energy_grad_mismatch(bad) > 1e-2
