@@ -452,12 +452,17 @@ def _autograd_step(os3d, synth, steps, timed):
         f.grad = None
         weighted_energy(orientation_score(f, bank), wt).backward()
 
+    def step_stored():
+        f.grad = None
+        score_energy(f, bank, wt, sweep=False).backward()
+
     def step():
         f.grad = None
         score_energy(f, bank, wt).backward()
 
     ms_torch = timed(step_torch_loss, max(2, steps // 2))
     ms_energy = timed(step_energy, max(2, steps // 2))
+    ms_stored = timed(step_stored, max(2, steps // 2))
     os3d.os3d_profile_reset()
     os3d.os3d_profile_enable(True)
     ms = timed(step, max(2, steps // 2))
@@ -476,20 +481,21 @@ def _autograd_step(os3d, synth, steps, timed):
     vo = B * int(np.prod(dims)) * len(V)
     del f, wt, U, g, fd
     torch.cuda.empty_cache()
-    # the energy kernel streams the score and the weights: 12 bytes per
-    # complex element (the weighted adjoint reads the same 12 bytes in its
-    # plane pass instead of an 8-byte stored gradient)
-    n, tot = prof["weighted_energy"]
-    k_ms = tot / max(n, 1)
-    ek = {"kernel_ms": k_ms, "gbs": vo * 12 / (k_ms / 1e3) / 1e9}
+    kinds = {k: v for k, v in prof.items() if v[0] > 0}
+    calls = max(prof["weighted_energy"][0], 1)   # one final energy sum per step
     return {"ms": ms, "value": vo / (ms / 1e3), "unit": UNIT,
-            "what": "score_energy: forward + weighted energy kernel + weighted adjoint "
-                    "(gradient 2 g w U folded into the plane pass), batch 8",
+            "what": "score_energy: one sweep per block (forward z-pass, plane pass forming U "
+                    "in shared memory, summing w|U|^2 and weighting it by 2w, adjoint "
+                    "z-pass), no stored score; backward scales the gradient by g; batch 8",
+            "kernels_per_step": {k: {"launches": v[0] / calls, "ms": v[1] / calls}
+                                 for k, v in kinds.items()},
+            "stored_score_ms": ms_stored,
+            "stored_score_what": "score_energy(sweep=False): os3d_forward, weighted energy "
+                                 "kernel, weighted adjoint (2 g w U folded into the plane pass)",
             "energy_then_adjoint_ms": ms_energy,
             "energy_then_adjoint_what": "orientation_score + weighted_energy: the gradient "
                                         "2 g w U stored, then os3d_adjoint",
             "torch_loss_ms": ms_torch, "torch_loss_value": vo / (ms_torch / 1e3),
-            "weighted_energy_kernel": ek,
             "transforms_ms": ms_t, "transforms_value": vo / (ms_t / 1e3)}
 
 

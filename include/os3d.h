@@ -167,6 +167,39 @@ os3d_status os3d_adjoint_weighted(const os3d_bank* bank, const void* U, const fl
                                   const float* g, os3d_udtype udtype, int batch, float* grad_f,
                                   void* workspace, void* stream);
 
+/* Weighted energy of the score of an image and its gradient in one sweep,
+ * without storing the score: L = sum w |W f|^2 (the weighted squared
+ * L_2(R^3 x S^2) norm of Sec. 2) and grad_f = Re W^*(2 g w W f), its gradient
+ * with respect to the real image f scaled by g, for `batch` volumes f
+ * (device float, batch x nz x ny x nx). Per block of orientation pairs the
+ * forward z-pass, one plane pass that forms U_a = W f in shared memory, sums
+ * (w_a + w_b) |U_a|^2 and replaces U_a by 2 g (w_a + w_b) U_a (U_b = conj U_a,
+ * w real), and the adjoint's z-pass (the structure of os3d_upsilon with the
+ * soft threshold replaced by the weighting). w (device float, the score's
+ * layout: batch x N_o x nz x ny x nx, 16-byte aligned); g (device float) or
+ * NULL for 1. `scratch` (device, at least os3d_score_energy_scratch doubles,
+ * 8-byte aligned, not shared with a concurrent call): scratch[0] receives L in
+ * double precision (one FP64 sum per plane and orientation pair, added in
+ * index order: bit-identical from call to call), `loss` (device float or NULL)
+ * L rounded to float. Square planes up to 128^2 (those of os3d_upsilon's fused
+ * plane pass); elsewhere EUNSUPPORTED (os3d_forward, os3d_weighted_energy and
+ * os3d_adjoint_weighted or os3d_adjoint give the same results). Errors:
+ * EINVAL, EUNSUPPORTED, ECUDA. */
+os3d_status os3d_score_energy_grad(const os3d_bank* bank, const float* f, const float* w,
+                                   const float* g, int batch, float* loss, float* grad_f,
+                                   double* scratch, size_t scratch_doubles, void* workspace,
+                                   void* stream);
+
+/* Doubles of scratch os3d_score_energy_grad needs for `batch` volumes:
+ * 1 + batch x (orientation pairs and unpaired orientations) x nz. */
+os3d_status os3d_score_energy_scratch(const os3d_bank* bank, int batch, size_t* doubles);
+
+/* y = g x over `count` floats (device, 16-byte aligned; y may be x), g read
+ * on the device: the chain-rule factor of an upstream gradient. Errors:
+ * EINVAL, ECUDA. */
+os3d_status os3d_scale_by(const float* x, float* y, long long count, const float* g,
+                          void* stream);
+
 /* Approximate reconstruction (Eq. Reconstruction2Approximation):
  * f_out = w Re sum_i U_i with the discrete measure w = 1 / (N_o c_0), the
  * value that makes the orientation sum of the wavelets exactly 1 at w = 0

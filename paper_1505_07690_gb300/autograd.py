@@ -10,16 +10,20 @@ weighted_energy(U, w) = sum w |U|^2, the (weighted) squared L_2(R^3 x S^2)
 norm of a score (Sec. 2, the norm-preservation identity), in one streaming
 kernel, with the gradient 2 g w U in another.
 
-score_energy(f, bank, w) = sum w |W f|^2 in one Function: its backward is the
-weighted adjoint Re W^*(2 g w U), which weights U inside the transform's load
-and never stores the score-sized gradient.
+score_energy(f, bank, w) = sum w |W f|^2 in one Function. On square planes up
+to 128^2 its forward is one sweep (os3d_score_energy_grad) that yields the
+loss and the gradient for g = 1 without storing the score, and its backward
+scales that gradient by g; elsewhere the forward stores U and the backward is
+the weighted adjoint Re W^*(2 g w U), which weights U inside the transform's
+load and never stores the score-sized gradient.
 """
 from __future__ import annotations
 
 import torch
 
 from .os3d import (OS3D_EUNSUPPORTED, Bank, OS3DError, os3d_adjoint, os3d_adjoint_weighted,
-                   os3d_forward, os3d_weighted_energy, os3d_weighted_energy_grad)
+                   os3d_forward, os3d_scale_by, os3d_score_energy_grad, os3d_weighted_energy,
+                   os3d_weighted_energy_grad)
 
 
 class OrientationScore(torch.autograd.Function):
@@ -72,19 +76,32 @@ def weighted_energy(U: torch.Tensor, w: torch.Tensor | None = None) -> torch.Ten
 
 class ScoreEnergy(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, f: torch.Tensor, bank: Bank, w: torch.Tensor):
+    def forward(ctx, f: torch.Tensor, bank: Bank, w: torch.Tensor, sweep: bool = True):
         ctx.bank = bank
         ctx.in_shape = f.shape
         fc = f.contiguous()
-        U = os3d_forward(bank, fc)
         wc = w.contiguous()
+        if sweep:
+            try:
+                loss, grad = os3d_score_energy_grad(bank, fc, wc)
+                ctx.sweep = True
+                ctx.save_for_backward(grad)
+                return loss
+            except OS3DError as e:
+                if e.status != OS3D_EUNSUPPORTED:
+                    raise
+        ctx.sweep = False
+        U = os3d_forward(bank, fc)
         ctx.save_for_backward(U, wc)
         return os3d_weighted_energy(U, wc)
 
     @staticmethod
     def backward(ctx, g: torch.Tensor):
-        U, w = ctx.saved_tensors
         gs = g.reshape(()).float().contiguous()
+        if ctx.sweep:
+            (grad,) = ctx.saved_tensors
+            return os3d_scale_by(grad, gs).reshape(ctx.in_shape), None, None, None
+        U, w = ctx.saved_tensors
         try:
             grad = os3d_adjoint_weighted(ctx.bank, U, w, gs)
         except OS3DError as e:
@@ -92,14 +109,16 @@ class ScoreEnergy(torch.autograd.Function):
                 raise
             # planes outside the plane pass: the gradient G = 2 g w U stored
             grad = os3d_adjoint(ctx.bank, os3d_weighted_energy_grad(U, w, gs))
-        return grad.reshape(ctx.in_shape), None, None
+        return grad.reshape(ctx.in_shape), None, None, None
 
 
-def score_energy(f: torch.Tensor, bank: Bank, w: torch.Tensor) -> torch.Tensor:
+def score_energy(f: torch.Tensor, bank: Bank, w: torch.Tensor, sweep: bool = True) -> torch.Tensor:
     """Differentiable L = sum w |W f|^2 for float32 CUDA volumes f of shape
     (nz, ny, nx) or (batch, nz, ny, nx) and constant float32 weights w of the
     score's shape ((batch,) N_o, nz, ny, nx); equal to
-    weighted_energy(orientation_score(f, bank), w) with a fused backward."""
+    weighted_energy(orientation_score(f, bank), w). sweep=True computes the
+    gradient with the loss in one sweep that stores no score (square planes up
+    to 128^2); sweep=False, or other planes, store U for the weighted adjoint."""
     if w.requires_grad:
         raise ValueError("score_energy differentiates f only; w must not require grad")
-    return ScoreEnergy.apply(f, bank, w)
+    return ScoreEnergy.apply(f, bank, w, sweep)

@@ -1069,6 +1069,63 @@ os3d_status upsilon_impl(const os3d_bank* b, const float* f, int batch, float* f
   return OS3D_OK;
 }
 
+// Weighted energy L = sum w |W f|^2 and its gradient Re W^*(2 g w W f) in one
+// sweep per block: the z-pass of the forward transform, the weighted
+// score-domain step (per-unit energies into scratch[1 ..]), the z-pass of the
+// adjoint; then the final sum of the unit energies in index order.
+long long energy_units(const os3d_bank* b, int batch) {
+  return (long long)batch * (long long)b->slot_a.size() * b->dims[0];
+}
+
+os3d_status score_energy_impl(const os3d_bank* b, const float* f, const float* wgt,
+                              const float* g, int batch, float* loss, float* grad_f,
+                              double* scratch, void* ws, cudaStream_t s) {
+  Work w;
+  if (const os3d_status e = workspace_for(b, ws, &w)) return e;
+  const int nz = b->dims[0], ny = b->dims[1], nx = b->dims[2];
+  const int nslots = (int)b->slot_a.size();
+  const int tiles = ny * (nx / kTileX);
+  for (int v = 0; v < batch; ++v) {
+    const os3d_status st = prep_fhat(b, f, v, w, s);
+    if (st != OS3D_OK) return st;
+    if (b->p.overlap) OS3D_CK(fork_side(b, s));
+    int q = 0;
+    for (int s0 = 0; s0 < nslots; s0 += b->block_slots, ++q) {
+      const int ns = std::min(b->block_slots, nslots - s0);
+      const int k = b->p.overlap ? (q & 1) : 0;
+      cudaStream_t st2 = b->p.overlap ? b->side[k] : s;
+      PassArgs za = args_base(b);
+      set_slots(b, za, v, s0, ns);
+      za.in = w.fh;
+      za.out = w.T[k];
+      OS3D_CK(counted_launch(OS3D_KIND_Z_FWD_SCORE, st2,
+                             [&] { return launch_z(nz, Z_FWD_SCORE, b->ev, za, tiles, st2); }));
+      PassArgs xa = za;
+      xa.in = w.T[k];
+      xa.out = w.T[k];
+      xa.wgt = wgt;
+      xa.gscale = g;
+      xa.epart = scratch + 1;
+      xa.epart_base = ((long long)v * nslots + s0) * nz;
+      OS3D_CK(counted_launch(OS3D_KIND_XY_SOFT, st2,
+                             [&] { return launch_xy(ny, nx, XY_WENERGY, 0, xa, st2); }));
+      PassArgs zi = za;
+      zi.in = w.T[k];
+      zi.out = w.A[k];
+      zi.accumulate = b->p.overlap ? q >= 2 : q >= 1;
+      OS3D_CK(counted_launch(OS3D_KIND_Z_INV_SCORE, st2,
+                             [&] { return launch_z(nz, Z_INV_SCORE, b->ev, zi, tiles, st2); }));
+    }
+    if (b->p.overlap) OS3D_CK(join_side(b, s));
+    const os3d_status st3 = finish_real(b, w, q, b->Gs, grad_f, v, s);
+    if (st3 != OS3D_OK) return st3;
+  }
+  OS3D_CK(counted_launch(OS3D_KIND_ENERGY, s, [&] {
+    return launch_energy_final(scratch, energy_units(b, batch), loss, s);
+  }));
+  return OS3D_OK;
+}
+
 // Linear diffusion with the propagator product on the tensor cores (sets of
 // more than kMaxOrientE orientations): E and the orientations go to the
 // device in the kernel's layout (in the workspace's second block
@@ -1164,6 +1221,40 @@ os3d_status os3d_adjoint_weighted(const os3d_bank* b, const void* U, const float
     return OS3D_EINVAL;
   if (udtype != OS3D_U_C64 || !xy_supported(b->dims[1], b->dims[2])) return OS3D_EUNSUPPORTED;
   return backward_impl(b, U, udtype, batch, grad_f, ws, (cudaStream_t)stream, false, w, g);
+}
+
+os3d_status os3d_score_energy_scratch(const os3d_bank* b, int batch, size_t* doubles) {
+  if (!b || batch < 1 || !doubles) return OS3D_EINVAL;
+  *doubles = (size_t)(1 + energy_units(b, batch));
+  return OS3D_OK;
+}
+
+os3d_status os3d_score_energy_grad(const os3d_bank* b, const float* f, const float* w,
+                                   const float* g, int batch, float* loss, float* grad_f,
+                                   double* scratch, size_t scratch_doubles, void* ws,
+                                   void* stream) {
+  const os3d_status st = check_call(b, f, grad_f, batch, OS3D_U_C64, ws);
+  if (st != OS3D_OK) return st;
+  if (!w || !scratch || (reinterpret_cast<uintptr_t>(w) & 15) ||
+      (reinterpret_cast<uintptr_t>(scratch) & 7) || (reinterpret_cast<uintptr_t>(g) & 3) ||
+      (reinterpret_cast<uintptr_t>(loss) & 3))
+    return OS3D_EINVAL;
+  if (scratch_doubles < (size_t)(1 + energy_units(b, batch))) return OS3D_EINVAL;
+  if (!soft_plane_supported(b->dims[1], b->dims[2])) return OS3D_EUNSUPPORTED;
+  return score_energy_impl(b, f, w, g, batch, loss, grad_f, scratch, ws, (cudaStream_t)stream);
+}
+
+os3d_status os3d_scale_by(const float* x, float* y, long long count, const float* g,
+                          void* stream) {
+  if (count < 0 || (count > 0 && (!x || !y || !g)) ||
+      ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(y)) & 15) ||
+      (reinterpret_cast<uintptr_t>(g) & 3))
+    return OS3D_EINVAL;
+  if (count == 0) return OS3D_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  OS3D_CK(counted_launch(OS3D_KIND_ENERGY_GRAD, s,
+                         [&] { return launch_scale_by(x, y, count, g, s); }));
+  return OS3D_OK;
 }
 
 os3d_status os3d_approx_reconstruct(const os3d_bank* b, const void* U, os3d_udtype udtype,

@@ -163,9 +163,9 @@ energy_partial_kernel(const void* __restrict__ U, const float* __restrict__ w, l
 }
 
 __global__ void __launch_bounds__(kThreads)
-energy_final_kernel(double* __restrict__ scratch, int nblocks, float* __restrict__ loss) {
+energy_final_kernel(double* __restrict__ scratch, long long nblocks, float* __restrict__ loss) {
   double a = 0.0;
-  for (int i = threadIdx.x; i < nblocks; i += kThreads) a += scratch[1 + i];
+  for (long long i = threadIdx.x; i < nblocks; i += kThreads) a += scratch[1 + i];
   const double t = block_sum(a);
   if (threadIdx.x == 0) {
     scratch[0] = t;
@@ -206,6 +206,24 @@ energy_grad_kernel(const void* U, const float* __restrict__ w, const float* __re
              make_float4(c.z * b.x, c.z * b.y, c.w * b.z, c.w * b.w));
     }
   }
+}
+
+// y = g x (y may be x)
+__global__ void __launch_bounds__(kThreads)
+scale_by_kernel(const float* x, float* y, long long count, const float* __restrict__ g) {
+  const float c = __ldg(g);
+  const long long stride = (long long)gridDim.x * kThreads;
+  const long long nq = count / 4;
+  for (long long q = (long long)blockIdx.x * kThreads + threadIdx.x; q < nq; q += stride) {
+    float4 v = reinterpret_cast<const float4*>(x)[q];
+    v.x *= c;
+    v.y *= c;
+    v.z *= c;
+    v.w *= c;
+    reinterpret_cast<float4*>(y)[q] = v;
+  }
+  const long long i = 4 * nq + threadIdx.x;
+  if (blockIdx.x == 0 && i < count) y[i] = c * x[i];
 }
 
 int sm_count() {
@@ -271,6 +289,17 @@ cudaError_t launch_energy(const void* U, const float* w, int ubf16, long long co
                       : launch_energy_t<1, 0>(U, w, nq, scratch, loss, s);
   return w ? launch_energy_t<0, 1>(U, w, nq, scratch, loss, s)
            : launch_energy_t<0, 0>(U, w, nq, scratch, loss, s);
+}
+
+cudaError_t launch_energy_final(double* scratch, long long n, float* loss, cudaStream_t s) {
+  energy_final_kernel<<<1, kThreads, 0, s>>>(scratch, n, loss);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scale_by(const float* x, float* y, long long count, const float* g,
+                            cudaStream_t s) {
+  scale_by_kernel<<<grid_for(std::max(1LL, count / 4)), kThreads, 0, s>>>(x, y, count, g);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_energy_grad(const void* U, const float* w, int ubf16, long long count,

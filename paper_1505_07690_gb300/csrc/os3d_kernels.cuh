@@ -38,8 +38,11 @@ enum ZMode { Z_FWD_PREP = 0, Z_FWD_SCORE = 1, Z_INV_SCORE = 2, Z_INV_FINAL = 3 }
 //                (Phi the soft threshold |u|^p sgn(u) per part, m_s = 2 for a pair)
 // XY_INV_WSCORE: XY_INV_SCORE on the weighted input 2 g (w_a U_a + conj(w_b U_b))
 // (the gradient of g sum w |U|^2, folded into the load; complex64 U)
+// XY_WENERGY: XY_SOFT with m_s Phi replaced by 2 g (w_a + w_b) (the gradient of
+// g sum w |U|^2 for U_b = conj U_a), sum (w_a + w_b) |U_a|^2 of each unit into
+// epart[epart_base + unit]
 enum XYMode { XY_FWD_REAL = 0, XY_FWD_SCORE = 1, XY_INV_SCORE = 2, XY_INV_REAL = 3, XY_SOFT = 4,
-              XY_INV_WSCORE = 5 };
+              XY_INV_WSCORE = 5, XY_WENERGY = 6 };
 
 struct PassArgs {
   const void* in;
@@ -60,8 +63,11 @@ struct PassArgs {
                               // skipped by the z-passes and read as zero / not written
                               // by the plane passes (cluster plane path only)
   float nvec[kMaxSlots][3];   // orientation n_a (x, y, z) of each slot
-  const float* wgt;           // XY_INV_WSCORE: weight per element, U's layout
-  const float* gscale;        // XY_INV_WSCORE: the scalar g (device)
+  const float* wgt;           // XY_INV_WSCORE, XY_WENERGY: weight per element, U's layout
+  const float* gscale;        // XY_INV_WSCORE, XY_WENERGY: the scalar g (device; or null
+                              // for 1 in XY_WENERGY)
+  double* epart;              // XY_WENERGY: per-unit energy sums
+  long long epart_base;       // XY_WENERGY: index of this launch's first unit
   HEval h;
 };
 
@@ -112,6 +118,11 @@ cudaError_t launch_energy(const void* U, const float* w, int ubf16, long long co
                           double* scratch, float* loss, cudaStream_t s);
 cudaError_t launch_energy_grad(const void* U, const float* w, int ubf16, long long count,
                                const float* g, void* G, cudaStream_t s);
+// the sum of scratch[1 .. n] in index order into scratch[0] and *loss
+cudaError_t launch_energy_final(double* scratch, long long n, float* loss, cudaStream_t s);
+// y = *g x over count floats (y may be x)
+cudaError_t launch_scale_by(const float* x, float* y, long long count, const float* g,
+                            cudaStream_t s);
 // in place on a.nslots volumes of a.out, a.slot_stride apart, nvox each;
 // slot s scaled by 2 when a.ub[s] >= 0 (an antipodal pair)
 cudaError_t launch_soft_slots(const PassArgs& a, long long nvox, cudaStream_t s);

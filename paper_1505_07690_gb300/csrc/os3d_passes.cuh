@@ -620,7 +620,13 @@ xy_kernel(const __grid_constant__ PassArgs a) {
 // them through that map, exchanges back to rows, and the DFT along x writes
 // T_s.
 // ----------------------------------------------------------------------------
-template <int NY, int NX>
+// WEIGHTED = 1 (XY_WENERGY): the score-domain step of the gradient of the
+// weighted energy L = sum w |U|^2 instead: for the pair (a, b = -a) the
+// adjoint's input 2 g (w_a U_a + conj(w_b U_b)) is 2 g (w_a + w_b) U_a (w is
+// real and U_b = conj U_a), 2 g w_a U_a for an unpaired slot, and the energy
+// of the unit, sum (w_a + w_b) |U_a|^2, goes to epart (FP32 over a thread's
+// elements, FP64 over the block in a fixed order).
+template <int NY, int NX, int WEIGHTED>
 __global__ void __cluster_dims__(XYSplit<NY, NX>::NS, 1, 1)
     __launch_bounds__(XYCfg<NY, NX>::NT, XYSplit<NY, NX>::NS == 1 ? 1 : 2)
 xy_soft_kernel(const __grid_constant__ PassArgs a) {
@@ -629,6 +635,9 @@ xy_soft_kernel(const __grid_constant__ PassArgs a) {
   static_assert(NS <= 2, "a plane on one CTA or on a 2-CTA cluster");
   constexpr int R1x = C::R1x, R2x = C::R2x, R1y = C::R1y, R2y = C::R2y;
   constexpr int NT = C::NT, NYH = C::NYH, NXH = C::NXH;
+  __shared__ double ered[WEIGHTED ? NT / 32 : 1];   // WEIGHTED: the warps' energy sums
+  float c2 = 0.f;                    // WEIGHTED: 2 g
+  if constexpr (WEIGHTED) c2 = 2.f * (a.gscale ? __ldg(a.gscale) : 1.f);
 
   extern __shared__ __align__(16) float2 sm[];
   float2* work = sm;
@@ -729,7 +738,9 @@ xy_soft_kernel(const __grid_constant__ PassArgs a) {
       }
     }
     __syncthreads();
-    // ---- (4) IDFT along y, step 2: U_s; m_s Phi(U_s) back into the rows read
+    // ---- (4) IDFT along y, step 2: U_s; m_s Phi(U_s) (or the weighted
+    // gradient) back into the rows read
+    float en = 0.f;   // WEIGHTED: this thread's part of the unit's energy
 #pragma unroll 1
     for (int j = 0; j < C::JY3; ++j) {
       const int q = t + NT * j;
@@ -739,11 +750,35 @@ xy_soft_kernel(const __grid_constant__ PassArgs a) {
       for (int m = 0; m < R2y; ++m) w[m] = work[(m + R2y * k1) * C::PY + c];
       dft<R2y, +1>(w);
 #pragma unroll
-      for (int k2 = 0; k2 < R2y; ++k2)
-        work[(R2y * k1 + k2) * C::PY + c] =
-            make_float2(scale * soft_part(w[k2].x, a.power), scale * soft_part(w[k2].y, a.power));
+      for (int k2 = 0; k2 < R2y; ++k2) {
+        if constexpr (WEIGHTED) {
+          const long long e = (long long)z * P + (long long)(k1 + R1y * k2) * NX + h * NXH + c;
+          float ww = __ldcs(a.wgt + a.ua[s] + e);
+          if (a.ub[s] >= 0) ww += __ldcs(a.wgt + a.ub[s] + e);
+          en = fmaf(ww, fmaf(w[k2].x, w[k2].x, w[k2].y * w[k2].y), en);
+          work[(R2y * k1 + k2) * C::PY + c] = cscale(w[k2], c2 * ww);
+        } else {
+          work[(R2y * k1 + k2) * C::PY + c] = make_float2(scale * soft_part(w[k2].x, a.power),
+                                                          scale * soft_part(w[k2].y, a.power));
+        }
+      }
+    }
+    if constexpr (WEIGHTED) {
+      double d = (double)en;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) d += __shfl_down_sync(0xffffffffu, d, o);
+      if ((t & 31) == 0) ered[t >> 5] = d;
     }
     __syncthreads();
+    if constexpr (WEIGHTED) {
+      // ered is written again only after the barriers of the next unit
+      if (t == 0) {
+        double sum = 0.0;
+#pragma unroll
+        for (int i = 0; i < NT / 32; ++i) sum += ered[i];
+        a.epart[a.epart_base + (long long)u * NS + h] = sum;
+      }
+    }
     // ---- (5) DFT along y, step 1 (in place through the row map)
     {
       const int n2 = t / C::CW;
@@ -830,11 +865,11 @@ xy_soft_kernel(const __grid_constant__ PassArgs a) {
   plane_sync<NS>();   // no CTA leaves while its peer may still write into it
 }
 
-template <int NY, int NX>
+template <int NY, int NX, int WEIGHTED>
 cudaError_t launch_xy_soft_one(const PassArgs& a, cudaStream_t s) {
   using C = XYCfg<NY, NX>;
   constexpr int NS = XYSplit<NY, NX>::NS;
-  auto k = xy_soft_kernel<NY, NX>;
+  auto k = xy_soft_kernel<NY, NX, WEIGHTED>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)C::smem_bytes);
   if (e != cudaSuccess) return e;
@@ -917,7 +952,10 @@ cudaError_t launch_xy_n(int mode, int ub, const PassArgs& a, cudaStream_t s) {
       if (ub) return cudaErrorInvalidValue;
       return launch_xy_one<NY, NX, XY_INV_WSCORE, 0>(a, s);
     case XY_SOFT:
-      if constexpr (NX <= 128) return launch_xy_soft_one<NY, NX>(a, s);
+      if constexpr (NX <= 128) return launch_xy_soft_one<NY, NX, 0>(a, s);
+      else return cudaErrorInvalidValue;
+    case XY_WENERGY:
+      if constexpr (NX <= 128) return launch_xy_soft_one<NY, NX, 1>(a, s);
       else return cudaErrorInvalidValue;
     default: return cudaErrorInvalidValue;
   }

@@ -79,6 +79,10 @@ def lib():
         L.os3d_inverse.argtypes = [vp, vp, i, i, vp, vp, vp]
         L.os3d_adjoint.argtypes = [vp, vp, i, i, vp, vp, vp]
         L.os3d_adjoint_weighted.argtypes = [vp, vp, vp, vp, i, i, vp, vp, vp]
+        L.os3d_score_energy_grad.argtypes = [vp, vp, vp, vp, i, vp, vp, vp, ctypes.c_size_t,
+                                             vp, vp]
+        L.os3d_score_energy_scratch.argtypes = [vp, i, ctypes.POINTER(ctypes.c_size_t)]
+        L.os3d_scale_by.argtypes = [vp, vp, ctypes.c_longlong, vp, vp]
         L.os3d_bank_info.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t),
                                      ctypes.POINTER(ctypes.c_size_t)]
         L.os3d_bank_resident_bytes.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t)]
@@ -117,7 +121,8 @@ def lib():
                      "os3d_angular_propagator", "os3d_server_stats",
                      "os3d_bank_resident_bytes", "os3d_bank_wait_errors", "os3d_wait_selftest",
                      "os3d_weighted_energy", "os3d_weighted_energy_grad",
-                     "os3d_adjoint_weighted"):
+                     "os3d_adjoint_weighted", "os3d_score_energy_grad",
+                     "os3d_score_energy_scratch", "os3d_scale_by"):
             getattr(L, name).restype = i
         _lib = L
     return _lib
@@ -348,6 +353,61 @@ def os3d_adjoint_weighted(bank: Bank, U, w, g=None, grad_f=None, workspace=None,
     def fn(h, Up, ud, batch, out, ws, st):
         return lib().os3d_adjoint_weighted(h, Up, wp, _ptr(gc), ud, batch, out, ws, st)
     return _backward(fn, "os3d_adjoint_weighted", bank, U, grad_f, workspace, stream)
+
+
+def os3d_score_energy_scratch(bank: Bank, batch: int) -> int:
+    """Doubles of scratch os3d_score_energy_grad needs for `batch` volumes."""
+    n = ctypes.c_size_t(0)
+    _check(lib().os3d_score_energy_scratch(bank.handle, int(batch), ctypes.byref(n)),
+           "os3d_score_energy_scratch")
+    return int(n.value)
+
+
+def os3d_score_energy_grad(bank: Bank, f, w, g=None, grad_f=None, scratch=None,
+                           workspace=None, stream=None):
+    """(L, grad_f): L = sum w |W f|^2 as a 0-dim float32 CUDA tensor and
+    grad_f = Re W^*(2 g w W f), in one sweep that never stores the score
+    (square planes up to 128^2; OS3DError with OS3D_EUNSUPPORTED elsewhere)."""
+    import torch
+    if not (f.is_cuda and f.dtype == torch.float32 and f.is_contiguous()):
+        raise ValueError("f must be a contiguous float32 CUDA tensor")
+    batch = _batch_of(f, 3, bank.dims)
+    n = batch * bank.n_o * int(np.prod(bank.dims))
+    if not (w.is_cuda and w.dtype == torch.float32 and w.is_contiguous() and w.numel() == n):
+        raise ValueError("w must be a contiguous float32 CUDA tensor of the score's size")
+    if g is not None and not (g.is_cuda and g.dtype == torch.float32 and g.numel() == 1):
+        raise ValueError("g must be a one-element float32 CUDA tensor")
+    if grad_f is None:
+        grad_f = torch.empty_like(f)
+    need = os3d_score_energy_scratch(bank, batch)
+    if scratch is None:
+        scratch = torch.empty(need, dtype=torch.float64, device=f.device)
+    if not (scratch.is_cuda and scratch.dtype == torch.float64 and scratch.is_contiguous()
+            and scratch.numel() >= need):
+        raise ValueError("scratch must be a float64 CUDA tensor of os3d_score_energy_scratch")
+    loss = torch.empty((), dtype=torch.float32, device=f.device)
+    gp = ctypes.c_void_p(None) if g is None else _ptr(g.contiguous())
+    _check(lib().os3d_score_energy_grad(bank.handle, _ptr(f), _ptr(w), gp, batch, _ptr(loss),
+                                        _ptr(grad_f), _ptr(scratch), scratch.numel(),
+                                        _ws_ptr(workspace), _stream(stream)),
+           "os3d_score_energy_grad")
+    return loss, grad_f
+
+
+def os3d_scale_by(x, g, out=None, stream=None):
+    """g x (float32 CUDA tensor x, one-element float32 CUDA g); out may be x."""
+    import torch
+    if not (x.is_cuda and x.dtype == torch.float32 and x.is_contiguous()):
+        raise ValueError("x must be a contiguous float32 CUDA tensor")
+    if not (g.is_cuda and g.dtype == torch.float32 and g.numel() == 1):
+        raise ValueError("g must be a one-element float32 CUDA tensor")
+    if out is None:
+        out = torch.empty_like(x)
+    if out.dtype != x.dtype or out.shape != x.shape or not out.is_contiguous():
+        raise ValueError("out must match x")
+    _check(lib().os3d_scale_by(_ptr(x), _ptr(out), x.numel(), _ptr(g.contiguous()),
+                               _stream(stream)), "os3d_scale_by")
+    return out
 
 
 def os3d_approx_reconstruct(bank: Bank, U, f_out=None, stream=None):

@@ -112,6 +112,10 @@ def test_argument_errors_before_any_launch(L):
     assert L.os3d_inverse(None, None, 0, 1, None, None, None) == 1
     assert L.os3d_adjoint(None, None, 0, 1, None, None, None) == 1
     assert L.os3d_adjoint_weighted(None, None, None, None, 0, 1, None, None, None) == 1
+    assert L.os3d_score_energy_grad(None, None, None, None, 1, None, None, None, 0, None,
+                                    None) == 1
+    n = ctypes.c_size_t(0)
+    assert L.os3d_score_energy_scratch(None, 1, ctypes.byref(n)) == 1
     assert L.os3d_bank_info(None, None, None) == 1
     assert L.os3d_destroy_bank(None) == 1
     assert L.os3d_approx_reconstruct(None, None, 0, 1, None, None) == 1
@@ -142,6 +146,10 @@ def test_argument_errors_before_any_launch(L):
     assert L.os3d_weighted_energy_grad(a16, None, 0, 5, a16, a16, None) == 1
     assert L.os3d_weighted_energy_grad(a16, None, 2, 4, a16, a16, None) == 1
     assert L.os3d_weighted_energy_grad(None, None, 0, 0, None, None, None) == 0  # nothing to do
+    assert L.os3d_scale_by(a16, a16, -1, a16, None) == 1
+    assert L.os3d_scale_by(a16 + 4, a16, 4, a16, None) == 1
+    assert L.os3d_scale_by(a16, a16, 4, None, None) == 1
+    assert L.os3d_scale_by(None, None, 0, None, None) == 0
     d = os3d.os3d_default_diffusion()
     assert (d.t, d.steps, d.D11, d.D33, d.D44, d.sh_degree) == (10.0, 8, 0.0, 1.0, 0.01, 0)
     assert L.os3d_enhance_linear(None, None, 1, None, ctypes.byref(d), None, None) == 1

@@ -269,3 +269,106 @@ def test_score_energy_matches_the_composition_bit_for_bit_in_the_loss(M):
     assert l1.item() == l2.item()
     rel = float(torch.linalg.vector_norm(g1 - ft.grad) / torch.linalg.vector_norm(ft.grad))
     assert rel <= 2e-6
+
+
+# ---------------------------------------------------------------------------
+# one sweep: L = sum w |W f|^2 and Re W^*(2 g w W f) without a stored score
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("dims,subdiv,L,nvol,kw", [
+    ((32, 32, 32), 1, 12, 2, {}),
+    ((16, 128, 128), 1, 12, 1, {}),
+    ((48, 48, 48), 1, 16, 1, {"block_slots": 3}),
+    ((32, 32, 32), 1, 12, 2, {"block_slots": 8, "overlap": 0}),
+    ((16, 16, 16), 2, 8, 1, {}),
+])
+def test_score_energy_sweep_against_oracle(M, dims, subdiv, L, nvol, kw):
+    """Paired sets in several block sizes, with and without the two-stream
+    overlap, 162 orientations on 16^3, batch 2; g = 0.8."""
+    import torch
+    V = M.os3d_icosa_orientations(subdiv)
+    bank = M.os3d_make_wavelets(dims, V, M.os3d_default_params(L=L, **kw))
+    f = np.stack([synth.spline_tubes(dims, 4, seed=70 + v) for v in range(nvol)])
+    w = synth.score_weights((nvol, len(V)) + dims, seed=7)
+    g = torch.tensor(0.8, device="cuda")
+    loss, grad = M.os3d_score_energy_grad(bank, _cuda(f), _cuda(w), g)
+    grad = grad.cpu().numpy()
+    ob = O.Bank(dims, O.icosa_orientations(subdiv), O.Params(L=L))
+    L_ref = 0.0
+    for v in range(nvol):
+        Uo = O.forward(f[v], ob)
+        L_ref += O.weighted_energy(Uo, w[v])
+        ref = O.adjoint(O.weighted_energy_grad(Uo, w[v], 0.8), ob)
+        assert float(np.linalg.norm(grad[v] - ref) / np.linalg.norm(ref)) <= 1e-5, v
+        assert np.abs(grad[v] - ref).max() <= 2e-5 * np.abs(ref).max(), v
+    assert abs(loss.item() - L_ref) <= 2e-5 * L_ref
+
+
+def test_score_energy_sweep_unpaired_orientations(M):
+    """21 orientations without their antipodes: weight w_a alone per slot."""
+    dims = (32, 32, 32)
+    V = O.icosa_orientations(1)[:21].copy()
+    bank = M.os3d_make_wavelets(dims, V, M.os3d_default_params(L=12, block_slots=4))
+    f = synth.spline_tubes(dims, 4, seed=75)
+    w = synth.score_weights((21,) + dims, seed=8)
+    loss, grad = M.os3d_score_energy_grad(bank, _cuda(f), _cuda(w))
+    ob = O.Bank(dims, V, O.Params(L=12))
+    Uo = O.forward(f, ob)
+    ref = O.adjoint(O.weighted_energy_grad(Uo, w), ob)
+    g = grad.cpu().numpy()
+    assert float(np.linalg.norm(g - ref) / np.linalg.norm(ref)) <= 1e-5
+    Lo = O.weighted_energy(Uo, w)
+    assert abs(loss.item() - Lo) <= 2e-5 * Lo
+
+
+def test_score_energy_sweep_repeatable_and_autograd(M):
+    """Bit-identical loss and gradient from call to call; the autograd Function
+    on the sweep equals its stored-score form (sweep=False) within FP32
+    rounding, the loss within the FP32 rounding of the two summation orders."""
+    import torch
+    from paper_1505_07690_gb300.autograd import score_energy
+    dims = (64, 64, 64)
+    V = M.os3d_icosa_orientations(1)
+    bank = M.os3d_make_wavelets(dims, V, M.os3d_default_params(L=16))
+    f = _cuda(np.stack([synth.spline_tubes(dims, 5, seed=80 + v) for v in range(2)]))
+    w = _cuda(synth.score_weights((2, len(V)) + dims, seed=9))
+    scratch = torch.empty(M.os3d_score_energy_scratch(bank, 2), dtype=torch.float64, device="cuda")
+    outs = []
+    for _ in range(3):
+        loss, grad = M.os3d_score_energy_grad(bank, f, w, scratch=scratch)
+        outs.append((scratch[0].item(), grad.clone()))
+    assert all(o[0] == outs[0][0] for o in outs)
+    assert all(torch.equal(o[1], outs[0][1]) for o in outs)
+    assert M.os3d_score_energy_scratch(bank, 2) == 1 + 2 * 21 * 64
+    ft = f.clone().requires_grad_(True)
+    l1 = score_energy(ft, bank, w)
+    (3.0 * l1).backward()
+    g1 = ft.grad.clone()
+    ft.grad = None
+    l2 = score_energy(ft, bank, w, sweep=False)
+    (3.0 * l2).backward()
+    assert abs(l1.item() - l2.item()) <= 1e-6 * abs(l2.item())
+    assert float(torch.linalg.vector_norm(g1 - ft.grad) / torch.linalg.vector_norm(ft.grad)) <= 2e-6
+    assert torch.allclose(g1, 3.0 * outs[0][1], rtol=1e-6, atol=0)
+
+
+def test_score_energy_sweep_rejections(M):
+    import torch
+    V = M.os3d_icosa_orientations(1)
+    bank = M.os3d_make_wavelets((32, 48, 64), V, M.os3d_default_params(L=12))
+    f = torch.zeros((32, 48, 64), device="cuda")
+    w = torch.zeros((42, 32, 48, 64), device="cuda")
+    with pytest.raises(M.OS3DError) as e:
+        M.os3d_score_energy_grad(bank, f, w)
+    assert e.value.status == M.OS3D_EUNSUPPORTED
+    bank = M.os3d_make_wavelets((32, 32, 32), V, M.os3d_default_params(L=12))
+    f = torch.zeros((32, 32, 32), device="cuda")
+    w = torch.zeros((42, 32, 32, 32), device="cuda")
+    small = torch.empty(10, dtype=torch.float64, device="cuda")
+    vp = ctypes.c_void_p
+    st = M.lib().os3d_score_energy_grad(bank.handle, vp(f.data_ptr()), vp(w.data_ptr()), vp(None),
+                                        1, vp(None), vp(f.data_ptr()), vp(small.data_ptr()), 10,
+                                        vp(None), vp(None))
+    assert st == 1   # scratch smaller than os3d_score_energy_scratch
+    x = torch.arange(7, dtype=torch.float32, device="cuda")
+    y = M.os3d_scale_by(x, torch.tensor(-2.0, device="cuda"))
+    assert torch.equal(y, -2.0 * x)
