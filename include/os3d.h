@@ -181,17 +181,18 @@ os3d_status os3d_adjoint_weighted(const os3d_bank* bank, const void* U, const fl
  * 8-byte aligned, not shared with a concurrent call): scratch[0] receives L in
  * double precision (one FP64 sum per plane and orientation pair, added in
  * index order: bit-identical from call to call), `loss` (device float or NULL)
- * L rounded to float. Square planes up to 128^2 (those of os3d_upsilon's fused
- * plane pass); elsewhere EUNSUPPORTED (os3d_forward, os3d_weighted_energy and
- * os3d_adjoint_weighted or os3d_adjoint give the same results). Errors:
- * EINVAL, EUNSUPPORTED, ECUDA. */
+ * L rounded to float. Planes of the plane pass (square 16^2 to 128^2, 256^2,
+ * 128 x 160; those of os3d_upsilon's fused plane pass); elsewhere EUNSUPPORTED
+ * (os3d_forward, os3d_weighted_energy and os3d_adjoint_weighted or
+ * os3d_adjoint give the same results). Errors: EINVAL, EUNSUPPORTED, ECUDA. */
 os3d_status os3d_score_energy_grad(const os3d_bank* bank, const float* f, const float* w,
                                    const float* g, int batch, float* loss, float* grad_f,
                                    double* scratch, size_t scratch_doubles, void* workspace,
                                    void* stream);
 
 /* Doubles of scratch os3d_score_energy_grad needs for `batch` volumes:
- * 1 + batch x (orientation pairs and unpaired orientations) x nz. */
+ * 1 + batch x (orientation pairs and unpaired orientations) x nz x (CTAs per
+ * plane: 8 for 256^2 planes, else 1). */
 os3d_status os3d_score_energy_scratch(const os3d_bank* bank, int batch, size_t* doubles);
 
 /* y = g x over `count` floats (device, 16-byte aligned; y may be x), g read

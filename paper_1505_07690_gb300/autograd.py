@@ -81,6 +81,10 @@ class ScoreEnergy(torch.autograd.Function):
         ctx.in_shape = f.shape
         fc = f.contiguous()
         wc = w.contiguous()
+        if not ctx.needs_input_grad[0]:
+            # the loss alone: the forward transform and the energy kernel
+            ctx.sweep = False
+            return os3d_weighted_energy(os3d_forward(bank, fc), wc)
         if sweep:
             try:
                 loss, grad = os3d_score_energy_grad(bank, fc, wc)

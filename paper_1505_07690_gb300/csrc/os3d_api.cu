@@ -58,7 +58,9 @@ bool xy_supported(int ny, int nx) {
          (ny == 128 && nx == 160);
 }
 // planes the fused soft-threshold plane pass holds (2-CTA clusters)
-bool soft_plane_supported(int ny, int nx) { return ny == nx && xy_supported(ny, nx) && nx <= 128; }
+bool soft_plane_supported(int ny, int nx) { return xy_supported(ny, nx); }
+// CTAs per plane of the plane passes (the kernels' XYSplit)
+int plane_ctas(int ny, int nx) { return (ny == 256 && nx == 256) ? 8 : 1; }
 cudaError_t launch_z(int nz, int mode, int ev, const PassArgs& a, int tiles, cudaStream_t s) {
   switch (nz) {
     case 16: return launch_z_16(mode, ev, a, tiles, s);
@@ -1074,7 +1076,8 @@ os3d_status upsilon_impl(const os3d_bank* b, const float* f, int batch, float* f
 // score-domain step (per-unit energies into scratch[1 ..]), the z-pass of the
 // adjoint; then the final sum of the unit energies in index order.
 long long energy_units(const os3d_bank* b, int batch) {
-  return (long long)batch * (long long)b->slot_a.size() * b->dims[0];
+  return (long long)batch * (long long)b->slot_a.size() * b->dims[0] *
+         plane_ctas(b->dims[1], b->dims[2]);
 }
 
 os3d_status score_energy_impl(const os3d_bank* b, const float* f, const float* wgt,
@@ -1106,7 +1109,7 @@ os3d_status score_energy_impl(const os3d_bank* b, const float* f, const float* w
       xa.wgt = wgt;
       xa.gscale = g;
       xa.epart = scratch + 1;
-      xa.epart_base = ((long long)v * nslots + s0) * nz;
+      xa.epart_base = ((long long)v * nslots + s0) * nz * plane_ctas(ny, nx);
       OS3D_CK(counted_launch(OS3D_KIND_XY_SOFT, st2,
                              [&] { return launch_xy(ny, nx, XY_WENERGY, 0, xa, st2); }));
       PassArgs zi = za;

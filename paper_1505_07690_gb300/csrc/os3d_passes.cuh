@@ -1,8 +1,9 @@
 // Fused DFT passes of the orientation-score transform (sm_103a).
 //
 // The 3D DFT of every orientation is split into a z-pass (DFT along z of
-// 16-wide pencil tiles) and an xy-pass (2D DFT of z-planes on a 2-CTA
-// cluster), with the per-orientation intermediate T held in L2:
+// 16-wide pencil tiles) and an xy-pass (2D DFT of z-planes: a whole plane per
+// CTA, or an 8-CTA cluster per 256^2 plane), with the per-orientation
+// intermediate T passed through L2:
 //   forward  (Eq. construction1Discrete):  U_a = IDFT_xy IDFT_z [ f_hat G h_a ]
 //            z-pass : f_hat tile (read once per block) x h(w_hat . n_a) -> IDFT_z -> T_a
 //            xy-pass: T_a -> IDFT_xy -> U_a and U_b = conj U_a           (HBM)
@@ -625,14 +626,14 @@ xy_kernel(const __grid_constant__ PassArgs a) {
 // adjoint's input 2 g (w_a U_a + conj(w_b U_b)) is 2 g (w_a + w_b) U_a (w is
 // real and U_b = conj U_a), 2 g w_a U_a for an unpaired slot, and the energy
 // of the unit, sum (w_a + w_b) |U_a|^2, goes to epart (FP32 over a thread's
-// elements, FP64 over the block in a fixed order).
+// elements, FP64 over the block in a fixed order; one sum per CTA of the
+// plane's cluster, at index unit x NS + rank).
 template <int NY, int NX, int WEIGHTED>
 __global__ void __cluster_dims__(XYSplit<NY, NX>::NS, 1, 1)
     __launch_bounds__(XYCfg<NY, NX>::NT, XYSplit<NY, NX>::NS == 1 ? 1 : 2)
 xy_soft_kernel(const __grid_constant__ PassArgs a) {
   using C = XYCfg<NY, NX>;
   constexpr int NS = XYSplit<NY, NX>::NS;
-  static_assert(NS <= 2, "a plane on one CTA or on a 2-CTA cluster");
   constexpr int R1x = C::R1x, R2x = C::R2x, R1y = C::R1y, R2y = C::R2y;
   constexpr int NT = C::NT, NYH = C::NYH, NXH = C::NXH;
   __shared__ double ered[WEIGHTED ? NT / 32 : 1];   // WEIGHTED: the warps' energy sums
@@ -646,7 +647,9 @@ xy_soft_kernel(const __grid_constant__ PassArgs a) {
 
   const int t = threadIdx.x;
   const int h = (int)cluster_rank();
-  const unsigned peer_base = NS == 1 ? 0u : map_cluster_rank(smem_addr(work), (unsigned)(h ^ 1));
+  unsigned peer_base[NS];   // the work buffer of every CTA of the cluster
+#pragma unroll
+  for (int q = 0; q < NS; ++q) peer_base[q] = map_cluster_rank(smem_addr(work), (unsigned)q);
   const long long P = (long long)NY * NX;
   const int cl = blockIdx.x / NS, ncl = gridDim.x / NS;
   const int nunits = a.nz * a.nslots;
@@ -710,10 +713,10 @@ xy_soft_kernel(const __grid_constant__ PassArgs a) {
 #pragma unroll
         for (int k2 = 0; k2 < R2x; ++k2) {
           const int c = k1 + R1x * k2;
-          const int owner = (NXH % R1x == 0) ? (k2 >= NXH / R1x) : (c >= NXH);
+          const int owner = (NXH % R1x == 0) ? (k2 / (NXH / R1x)) : (c / NXH);
           const int idx = row + c - owner * NXH;
           if (owner == h) work[idx] = w[j][k2];
-          else st_cluster_f2(peer_base + 8u * (unsigned)idx, w[j][k2]);
+          else st_cluster_f2(peer_base[owner] + 8u * (unsigned)idx, w[j][k2]);
         }
       }
       plane_sync<NS>();   // this CTA's y layout is complete
@@ -818,10 +821,10 @@ xy_soft_kernel(const __grid_constant__ PassArgs a) {
 #pragma unroll
         for (int k2 = 0; k2 < R2y; ++k2) {
           const int ky = k1 + R1y * k2;
-          const int owner = ky >= NYH;
+          const int owner = ky / NYH;
           const int idx = C::xphys(ky - owner * NYH, h * NXH + c);
           if (owner == h) work[idx] = w[j][k2];
-          else st_cluster_f2(peer_base + 8u * (unsigned)idx, w[j][k2]);
+          else st_cluster_f2(peer_base[owner] + 8u * (unsigned)idx, w[j][k2]);
         }
       }
       plane_sync<NS>();   // this CTA's x layout is complete
@@ -876,13 +879,16 @@ cudaError_t launch_xy_soft_one(const PassArgs& a, cudaStream_t s) {
   int dev = 0, nsm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  int per_sm = 1;
+  // a whole plane per CTA: as many CTAs as are resident at once; clusters:
+  // two CTAs per SM
+  int per_sm = 2;
   if constexpr (NS == 1) {
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, C::NT, C::smem_bytes);
     if (e != cudaSuccess) return e;
     per_sm = std::max(1, per_sm);
   }
-  const int clusters = std::max(1, std::min(a.nz * a.nslots, per_sm * nsm));
+  const int clusters =
+      std::max(1, std::min(a.nz * a.nslots, NS == 1 ? per_sm * nsm : per_sm * nsm / NS));
   k<<<NS * clusters, C::NT, C::smem_bytes, s>>>(a);
   return cudaGetLastError();
 }
@@ -951,12 +957,8 @@ cudaError_t launch_xy_n(int mode, int ub, const PassArgs& a, cudaStream_t s) {
     case XY_INV_WSCORE:
       if (ub) return cudaErrorInvalidValue;
       return launch_xy_one<NY, NX, XY_INV_WSCORE, 0>(a, s);
-    case XY_SOFT:
-      if constexpr (NX <= 128) return launch_xy_soft_one<NY, NX, 0>(a, s);
-      else return cudaErrorInvalidValue;
-    case XY_WENERGY:
-      if constexpr (NX <= 128) return launch_xy_soft_one<NY, NX, 1>(a, s);
-      else return cudaErrorInvalidValue;
+    case XY_SOFT: return launch_xy_soft_one<NY, NX, 0>(a, s);
+    case XY_WENERGY: return launch_xy_soft_one<NY, NX, 1>(a, s);
     default: return cudaErrorInvalidValue;
   }
 }

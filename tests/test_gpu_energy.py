@@ -280,10 +280,13 @@ def test_score_energy_matches_the_composition_bit_for_bit_in_the_loss(M):
     ((48, 48, 48), 1, 16, 1, {"block_slots": 3}),
     ((32, 32, 32), 1, 12, 2, {"block_slots": 8, "overlap": 0}),
     ((16, 16, 16), 2, 8, 1, {}),
+    ((16, 256, 256), 1, 12, 1, {}),
+    ((16, 128, 160), 1, 12, 2, {}),
 ])
 def test_score_energy_sweep_against_oracle(M, dims, subdiv, L, nvol, kw):
     """Paired sets in several block sizes, with and without the two-stream
-    overlap, 162 orientations on 16^3, batch 2; g = 0.8."""
+    overlap, 162 orientations on 16^3, batch 2, 256^2 planes on 8-CTA clusters
+    and 128 x 160 planes; g = 0.8."""
     import torch
     V = M.os3d_icosa_orientations(subdiv)
     bank = M.os3d_make_wavelets(dims, V, M.os3d_default_params(L=L, **kw))
@@ -349,6 +352,8 @@ def test_score_energy_sweep_repeatable_and_autograd(M):
     assert abs(l1.item() - l2.item()) <= 1e-6 * abs(l2.item())
     assert float(torch.linalg.vector_norm(g1 - ft.grad) / torch.linalg.vector_norm(ft.grad)) <= 2e-6
     assert torch.allclose(g1, 3.0 * outs[0][1], rtol=1e-6, atol=0)
+    with torch.no_grad():   # the loss alone takes the transform and the energy kernel
+        assert score_energy(f, bank, w).item() == l2.item()
 
 
 def test_score_energy_sweep_rejections(M):

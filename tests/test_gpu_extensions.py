@@ -179,6 +179,15 @@ def test_upsilon_unpaired_and_pencil_grid(M):
     _upsilon_check(M, dims, V, f, L=12, block_slots=4)
 
 
+@pytest.mark.parametrize("dims", [(16, 256, 256), (16, 128, 160)])
+def test_upsilon_cluster_and_rectangular_planes(M, dims):
+    """The fused score-domain plane kernel on 8-CTA clusters (256^2 planes,
+    exchanges through distributed shared memory) and on 128 x 160 planes (the
+    y direction's last pass of columns partial), against the oracle, p = 1.5."""
+    f = synth.straight_tubes(dims, 3, seed=31)
+    _upsilon_check(M, dims, O.icosa_orientations(1), f, L=12)
+
+
 def test_upsilon_equals_the_composition(M):
     """Fused Upsilon = os3d_forward, os3d_soft_threshold, os3d_inverse."""
     dims = (64, 64, 64)
