@@ -60,7 +60,8 @@ def _args():
     ap.add_argument("--only-step", action="store_true",
                     help="time the headline step alone (no end-to-end, per-kernel, operation, "
                          "serving, precision or CPU legs): for profiler captures")
-    ap.add_argument("--only-op", default="", choices=["", "enhance_linear_162", "upsilon", "autograd"],
+    ap.add_argument("--only-op", default="", choices=["", "enhance_linear_162", "upsilon", "autograd",
+                                                  "score_energy"],
                     help="time one operation alone on the headline grid (for profiler captures): "
                          "enhance_linear_162 = the linear diffusion with the 162-orientation bank; "
                          "upsilon = the fused soft-threshold processing (p = 1.5)")
@@ -969,7 +970,7 @@ def run_only_op(args):
     import torch
     from paper_1505_07690_gb300 import build, os3d, synth
     build.build()
-    if args.only_op == "autograd":
+    if args.only_op in ("autograd", "score_energy"):
         def timed(fn, n):
             for _ in range(max(args.warmup, 1)):
                 fn()
@@ -981,8 +982,28 @@ def run_only_op(args):
             b.record()
             torch.cuda.synchronize()
             return a.elapsed_time(b) / n
+    if args.only_op == "autograd":
         r = _autograd_step(os3d, synth, 2 * args.steps, timed)
         print(json.dumps({"op": "autograd", "workload": "splines96x8_no42", **r}), flush=True)
+        return 0
+    if args.only_op == "score_energy":
+        # the one-sweep loss and gradient on the first 2 volumes of the
+        # differentiation workload (weights 297 MB, larger than L2)
+        w = synth.WORKLOADS["splines96x8_no42"]
+        dims = w["shape"]
+        V = os3d.os3d_icosa_orientations(w["subdiv"])
+        bank = os3d.os3d_make_wavelets(dims, V, os3d.os3d_default_params(L=w["L"]))
+        f = torch.from_numpy(np.stack([synth.workload_volume("splines96x8_no42", batch_index=b)
+                                       for b in range(2)])).cuda()
+        wt = torch.from_numpy(synth.score_weights((8, len(V)) + tuple(dims), seed=1)[:2].copy()).cuda()
+        g = torch.empty_like(f)
+        scratch = torch.empty(os3d.os3d_score_energy_scratch(bank, 2), dtype=torch.float64,
+                              device="cuda")
+        ms = timed(lambda: os3d.os3d_score_energy_grad(bank, f, wt, grad_f=g, scratch=scratch),
+                   args.steps)
+        print(json.dumps({"op": "score_energy", "workload": "splines96x8_no42[:2]", "n_o": len(V),
+                          "ms": ms, "steps": args.steps, "loss": float(scratch[0].item())}),
+              flush=True)
         return 0
     w = synth.WORKLOADS[WORKLOAD]
     dims = w["shape"]

@@ -670,6 +670,16 @@ xy_soft_kernel(const __grid_constant__ PassArgs a) {
                   (unsigned)(NYH * NX * sizeof(float2)));
     }
     const float scale = a.ub[s] >= 0 ? 2.f : 1.f;
+    if constexpr (WEIGHTED) {
+      // this CTA's rows of the unit's weights go to L2 while the IDFT runs
+      // (the cluster's CTAs together cover the plane)
+      if (t == 32) {
+        const long long rows = (long long)z * P + (long long)h * NYH * NX;
+        constexpr unsigned wbytes = (unsigned)(NYH * NX) * 4u;
+        prefetch_l2(a.wgt + a.ua[s] + rows, wbytes);
+        if (a.ub[s] >= 0) prefetch_l2(a.wgt + a.ub[s] + rows, wbytes);
+      }
+    }
     // ---- (1) IDFT along x, step 1 (global -> registers -> shared)
     {
       const int n2 = t % R2x, r0 = t / R2x;
