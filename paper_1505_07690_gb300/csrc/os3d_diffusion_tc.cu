@@ -195,6 +195,11 @@ struct TcSplit {
     return wg == 0 ? 0 : wg == 1 ? (CG0 + 1) / 2 : wg == 2 ? CG0 : CG0 + (NCH - CG0 + 1) / 2;
   }
   static __host__ __device__ constexpr int end(int wg) { return wg == 3 ? NCH : begin(wg + 1); }
+  static __host__ __device__ constexpr int most() {   // most chunks of one warpgroup
+    int m = 0;
+    for (int w = 0; w < 4; ++w) m = end(w) - begin(w) > m ? end(w) - begin(w) : m;
+    return m;
+  }
   static_assert(N1 >= 16, "both MMA groups non-empty");
 };
 
@@ -364,48 +369,55 @@ __global__ void __launch_bounds__(512, 1) enhance_tc_kernel(const __grid_constan
       if (!mbar_wait_bounded(my_bar, phase)) lost = true;
       phase ^= 1u;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      // ---- W = F^2 D (F D after the last step), scales undone
+      // ---- W = F^2 D (F D after the last step), scales undone; this
+      // thread's chunks of W stay in registers until the row's scale is known
       const bool last = s == a.steps - 1;
       const float undo = a.inv_se / sq;
       float wmax = 0.f;
-#pragma unroll 1
-      for (int c0 = cbeg; c0 < cend; c0 += G) {
-        float d[G][16], f[G][16];
+      float wv[S::most()][16];
 #pragma unroll
-        for (int g = 0; g < G; ++g)
-          if (c0 + g < cend) {
-            tmem_ld16_async(tD + 16 * (c0 + g), d[g]);
-            tmem_ld16_async(tF + 16 * (c0 + g), f[g]);
-          }
-        tmem_wait<G>(d);
-        tmem_wait<G>(f);
+      for (int ci = 0; ci < S::most(); ++ci) {
+        const int c = cbeg + ci;
+        if (c >= cend) break;
+        float d[1][16], f[1][16];
+        tmem_ld16_async(tD + 16 * c, d[0]);
+        tmem_ld16_async(tF + 16 * c, f[0]);
+        tmem_wait<1>(d);
+        tmem_wait<1>(f);
 #pragma unroll
-        for (int g = 0; g < G; ++g) {
-          if (c0 + g >= cend) continue;
+        for (int jj = 0; jj < 16; ++jj) {
+          const float w = d[0][jj] * undo * (last ? f[0][jj] : f[0][jj] * f[0][jj]);
+          wv[ci][jj] = w;
+          wmax = fmaxf(wmax, fabsf(w));
+        }
+        if (last) {
 #pragma unroll
           for (int jj = 0; jj < 16; ++jj) {
-            const float w = d[g][jj] * undo * (last ? f[g][jj] : f[g][jj] * f[g][jj]);
-            d[g][jj] = w;
-            wmax = fmaxf(wmax, fabsf(w));
-          }
-          if (last) {
-#pragma unroll
-            for (int jj = 0; jj < 16; ++jj) {
-              const int i = 16 * (c0 + g) + jj;
-              if (vox >= 0 && i < a.n_o) {
-                const float tau = fmaf(wx, nv[3 * i], fmaf(wy, nv[3 * i + 1], wz * nv[3 * i + 2]));
-                msum = fmaf(h_of(tau), d[g][jj], msum);
-              }
+            const int i = 16 * c + jj;
+            if (vox >= 0 && i < a.n_o) {
+              const float tau = fmaf(wx, nv[3 * i], fmaf(wy, nv[3 * i + 1], wz * nv[3 * i + 2]));
+              msum = fmaf(h_of(tau), wv[ci][jj], msum);
             }
-          } else {
-            tmem_st16(tD + 16 * (c0 + g), d[g]);
           }
         }
       }
       if (!last) {
-        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-        sq = row_scale(row_reduce(wmax, true));
-        split_to_smem(sq);
+        // the row's maximum over the four warpgroups: one barrier (red is
+        // written again only after the next step's barrier)
+        red[wg * TV + q] = wmax;
+        __syncthreads();
+        float r = red[q];
+#pragma unroll
+        for (int g = 1; g < NWG; ++g) r = fmaxf(r, red[g * TV + q]);
+        sq = row_scale(r);
+#pragma unroll
+        for (int ci = 0; ci < S::most(); ++ci) {
+          const int c = cbeg + ci;
+          if (c >= cend) break;
+#pragma unroll
+          for (int jj = 0; jj < 16; ++jj) wv[ci][jj] *= sq;
+          store_split<NP>(sVhi, sVlo, q, c, wv[ci]);
+        }
       }
     }
     // m = h^T v: the warpgroups' partial sums of the row
