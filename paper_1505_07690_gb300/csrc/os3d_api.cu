@@ -1312,6 +1312,9 @@ os3d_status os3d_soft_threshold(const void* in, void* out, os3d_udtype udtype, l
   return OS3D_OK;
 }
 
+static_assert(OS3D_ENERGY_SCRATCH_DOUBLES == 1 + kMaxEnergyBlocks,
+              "the energy scratch holds the sum and one partial per block");
+
 os3d_status os3d_weighted_energy(const void* U, const float* w, os3d_udtype udtype,
                                  long long count, double* scratch, float* loss, void* stream) {
   if (!scratch || count < 0 || count % 4 != 0 || (count > 0 && !U)) return OS3D_EINVAL;
