@@ -20,6 +20,7 @@ import csv
 import hashlib
 import io
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -643,6 +644,13 @@ def run_ours(args):
                 "frac": None, "traffic": _ncu_traffic(dom), "launch_ms": ms / max(nl, 1)}
     # whole-step HBM view: U written once and read once
     step_bytes = 2 * n_o * nvox * esize + 4 * nvox * 4
+    # algorithmic FP32 flops per step: per orientation pair (antipodal
+    # pairing: one 3D transform per pair) and direction, a 3D DFT at
+    # 5 n^3 log2(n^3) (radix-2 convention) plus the wavelet at every point,
+    # 2 (L + 1) + 15 (Horner on L + 1 coefficients, the direction cosine, the
+    # radial factor and the product)
+    pairs = (n_o + 1) // 2
+    step_flops = 2.0 * pairs * nvox * (5.0 * math.log2(nvox) + 2 * (w["L"] + 1) + 15)
     kernels = {k: {"launches": v[0], "ms_per_step": v[1] / args.steps,
                    "share": v[1] / max(sum(x[1] for x in prof.values()), 1e-9)}
                for k, v in prof.items() if v[0]}
@@ -763,6 +771,8 @@ def run_ours(args):
         ops["precision"] = precision_leg(3, 3)
         ops["serving"] = serve_mix(300, 0.8, False)
 
+    fp32_peak_step = (torch.cuda.get_device_properties(local).multi_processor_count * 128 * 2 *
+                      (clk["sm_mhz"] if clk else 2070.0) * 1e6 / 1e12)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, fo, desc, cores = oracle_on_cores(WORKLOAD)
@@ -782,6 +792,11 @@ def run_ours(args):
             "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
             "roofline": roof,
             "step_hbm": {"bytes": step_bytes, "achieved_gbs": step_bytes / (total_ms / args.steps / 1e3) / 1e9},
+            "step_alu": {"flops": step_flops,
+                         "achieved_tflops": step_flops / (total_ms / args.steps / 1e3) / 1e12,
+                         "peak_tflops": fp32_peak_step,
+                         "frac": step_flops / (total_ms / args.steps / 1e3) / 1e12 / fp32_peak_step,
+                         "peak_kind": "FP32 CUDA-core FMA rate: SMs x 128 lanes x 2 x median SM clock"},
             "kernels": kernels,
             "ops": ops,
             "cpu_baseline": cpu,
