@@ -216,6 +216,22 @@ def test_weighted_adjoint_against_oracle(M, dims, L, nvol):
         assert float(np.linalg.norm(got[v] - two[v]) / np.linalg.norm(two[v])) <= 2e-6, v
 
 
+def test_weighted_adjoint_unpaired_orientations(M):
+    """21 orientations without their antipodes (each slot loads w_a U_a alone),
+    blocks of 4 slots, two volumes."""
+    import torch
+    dims = (32, 32, 32)
+    V = O.icosa_orientations(1)[:21].copy()
+    bank = M.os3d_make_wavelets(dims, V, M.os3d_default_params(L=12, block_slots=4))
+    U, w = _score((2, 21) + dims, seed=24)
+    got = M.os3d_adjoint_weighted(bank, _cuda(U), _cuda(w), torch.tensor(1.3, device="cuda"))
+    got = got.cpu().numpy()
+    ob = O.Bank(dims, V, O.Params(L=12))
+    for v in range(2):
+        ref = O.adjoint(O.weighted_energy_grad(U[v], w[v], 1.3), ob)
+        assert float(np.linalg.norm(got[v] - ref) / np.linalg.norm(ref)) <= 1e-5, v
+
+
 def test_weighted_adjoint_unsupported_forms_and_score_energy_fallback(M):
     """BF16 scores and planes without a plane pass (32 x 48 x 64 runs pencil
     passes) answer EUNSUPPORTED; score_energy then stores G = 2 g w U and
