@@ -10,12 +10,14 @@ weighted_energy(U, w) = sum w |U|^2, the (weighted) squared L_2(R^3 x S^2)
 norm of a score (Sec. 2, the norm-preservation identity), in one streaming
 kernel, with the gradient 2 g w U in another.
 
-score_energy(f, bank, w) = sum w |W f|^2 in one Function. On square planes up
-to 128^2 its forward is one sweep (os3d_score_energy_grad) that yields the
+score_energy(f, bank, w) = sum w |W f|^2 in one Function. On the planes of the
+plane pass its forward is one sweep (os3d_score_energy_grad) that yields the
 loss and the gradient for g = 1 without storing the score, and its backward
-scales that gradient by g; elsewhere the forward stores U and the backward is
-the weighted adjoint Re W^*(2 g w U), which weights U inside the transform's
-load and never stores the score-sized gradient.
+scales that gradient by g. With sweep=False the forward stores U and the
+backward is the weighted adjoint Re W^*(2 g w U), which weights U inside the
+transform's load and never stores the score-sized gradient; on planes the
+plane pass does not hold (pencil passes) the backward stores G = 2 g w U and
+takes os3d_adjoint.
 """
 from __future__ import annotations
 
@@ -121,8 +123,9 @@ def score_energy(f: torch.Tensor, bank: Bank, w: torch.Tensor, sweep: bool = Tru
     (nz, ny, nx) or (batch, nz, ny, nx) and constant float32 weights w of the
     score's shape ((batch,) N_o, nz, ny, nx); equal to
     weighted_energy(orientation_score(f, bank), w). sweep=True computes the
-    gradient with the loss in one sweep that stores no score (square planes up
-    to 128^2); sweep=False, or other planes, store U for the weighted adjoint."""
+    gradient with the loss in one sweep that stores no score (the planes of the
+    plane pass: square 16^2 to 128^2, 256^2, 128 x 160); sweep=False, or other
+    planes, store U for the weighted adjoint."""
     if w.requires_grad:
         raise ValueError("score_energy differentiates f only; w must not require grad")
     return ScoreEnergy.apply(f, bank, w, sweep)

@@ -57,7 +57,7 @@ bool xy_supported(int ny, int nx) {
           (nx == 16 || nx == 32 || nx == 48 || nx == 64 || nx == 96 || nx == 128 || nx == 256)) ||
          (ny == 128 && nx == 160);
 }
-// planes the fused soft-threshold plane pass holds (2-CTA clusters)
+// planes the fused score-domain plane pass holds (every plane of the plane pass)
 bool soft_plane_supported(int ny, int nx) { return xy_supported(ny, nx); }
 // CTAs per plane of the plane passes (the kernels' XYSplit)
 int plane_ctas(int ny, int nx) { return (ny == 256 && nx == 256) ? 8 : 1; }

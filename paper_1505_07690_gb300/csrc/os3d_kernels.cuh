@@ -29,7 +29,7 @@ struct HEval {
 //  Z_INV_SCORE: T_s -> DFT_z -> x h(w_hat . n_s), sum over slots  -> A
 //  Z_INV_FINAL: A x mult (G/(n^3 max(M,eps))) -> IDFT_z           -> T0
 enum ZMode { Z_FWD_PREP = 0, Z_FWD_SCORE = 1, Z_INV_SCORE = 2, Z_INV_FINAL = 3 };
-// xy-passes (2D DFT of z-planes, a 2-CTA cluster per plane):
+// xy-passes (2D DFT of z-planes: a whole plane per CTA, an 8-CTA cluster per 256^2 plane):
 //  XY_FWD_REAL : f (real) -> DFT_xy                                -> T0
 //  XY_FWD_SCORE: T_s -> IDFT_xy -> U_a, U_b = conj U_a              (HBM store)
 //  XY_INV_SCORE: U_a + conj U_b (HBM load) -> DFT_xy               -> T_s
@@ -61,7 +61,7 @@ struct PassArgs {
   float power;                // XY_SOFT / soft threshold: exponent p > 0
   int disc;                   // 1: 16-column z tiles outside the disc |w_xy| < pi are
                               // skipped by the z-passes and read as zero / not written
-                              // by the plane passes (cluster plane path only)
+                              // by the plane passes (not by the pencil passes)
   float nvec[kMaxSlots][3];   // orientation n_a (x, y, z) of each slot
   const float* wgt;           // XY_INV_WSCORE, XY_WENERGY: weight per element, U's layout
   const float* gscale;        // XY_INV_WSCORE, XY_WENERGY: the scalar g (device; or null

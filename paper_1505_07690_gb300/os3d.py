@@ -367,7 +367,8 @@ def os3d_score_energy_grad(bank: Bank, f, w, g=None, grad_f=None, scratch=None,
                            workspace=None, stream=None):
     """(L, grad_f): L = sum w |W f|^2 as a 0-dim float32 CUDA tensor and
     grad_f = Re W^*(2 g w W f), in one sweep that never stores the score
-    (square planes up to 128^2; OS3DError with OS3D_EUNSUPPORTED elsewhere)."""
+    (planes of the plane pass: square 16^2 to 128^2, 256^2 and 128 x 160;
+    OS3DError with OS3D_EUNSUPPORTED elsewhere)."""
     import torch
     if not (f.is_cuda and f.dtype == torch.float32 and f.is_contiguous()):
         raise ValueError("f must be a contiguous float32 CUDA tensor")
