@@ -155,8 +155,10 @@ os3d_status os3d_inverse(const os3d_bank* bank, const void* U, os3d_udtype udtyp
 os3d_status os3d_adjoint(const os3d_bank* bank, const void* G, os3d_udtype udtype, int batch,
                          float* grad_f, void* workspace, void* stream);
 
-/* Weighted adjoint: grad_f = Re W^*(2 g w U), the gradient with respect to a
- * real image f of g sum w |U|^2 at U = W f (os3d_weighted_energy), i.e.
+/* Weighted adjoint (the adjoint of Sec. 4.1 and App. A applied to the
+ * gradient of the weighted energy): grad_f = Re W^*(2 g w U), the gradient
+ * with respect to a real image f of g sum w |U|^2 at U = W f (see
+ * os3d_weighted_energy), i.e.
  * os3d_adjoint of os3d_weighted_energy_grad's G without G being stored: the
  * plane pass multiplies each element of U by 2 g w as it loads it. U (device,
  * batch complex64 scores), w (device float, one weight per complex element,
