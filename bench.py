@@ -174,6 +174,68 @@ def _ow_transform_part(job):
     return slot
 
 
+def _ow_init_in(dims, orients, L, shm_in):
+    import numpy as np
+    from multiprocessing import shared_memory
+    from oracle import os3d_oracle as O
+    _OW["O"] = O
+    _OW["bank"] = O.Bank(dims, orients, O.Params(L=L))
+    _OW["shm"] = (shared_memory.SharedMemory(name=shm_in),)
+    _OW["f"] = np.ndarray(dims, np.float64, buffer=_OW["shm"][0].buf)
+
+
+def _ow_sample_part(i):
+    """The oracle's forward transform of the shared volume for orientation i
+    and that orientation's part of the inverse's orientation sum; (seconds,
+    checksum)."""
+    import numpy as np
+    O, bank = _OW["O"], _OW["bank"]
+    t0 = time.perf_counter()
+    U = O.forward(_OW["f"], bank, [i])
+    acc = O.backproject(U, bank, [i])
+    return time.perf_counter() - t0, float(np.abs(acc).sum())
+
+
+def oracle_sample_on_cores(workload, cores=None):
+    """The oracle on a bounded sample of a large workload: one orientation per
+    single-threaded process (as many as host cores and memory allow, about
+    2 GB each at 256^3), each the forward transform of the whole volume and
+    its part of the inverse's orientation sum. (voxel-orientations/s over the
+    slowest process's time, description, processes)."""
+    import multiprocessing as mp
+    import numpy as np
+    from multiprocessing import shared_memory
+    from oracle import os3d_oracle as O
+    from paper_1505_07690_gb300 import synth
+    w = synth.WORKLOADS[workload]
+    dims = tuple(w["shape"])
+    nvox = int(np.prod(dims))
+    V = O.icosa_orientations(w["subdiv"])
+    try:
+        ram = os.sysconf("SC_PHYS_PAGES") * os.sysconf("SC_PAGE_SIZE")
+    except (ValueError, OSError):
+        ram = 0
+    per_proc = 16 * nvox * 8          # the volume and its transforms in complex128
+    n = max(1, min(cores or os.cpu_count() or 1, len(V), int(0.3 * ram // per_proc) or 1))
+    f = synth.workload_volume(workload).astype(np.float64)
+    shm = shared_memory.SharedMemory(create=True, size=nvox * 8)
+    try:
+        np.ndarray(dims, np.float64, buffer=shm.buf)[...] = f
+        with mp.get_context("spawn").Pool(n, initializer=_ow_init_in,
+                                          initargs=(dims, V, w["L"], shm.name)) as pool:
+            res = pool.map(_ow_sample_part, list(range(n)), chunksize=1)
+    finally:
+        shm.close()
+        shm.unlink()
+    t = max(r[0] for r in res)
+    grid = "x".join(str(d) for d in dims)
+    desc = (f"{n} of the {len(V)} orientations of the whole {grid} volume ({workload}): per "
+            f"orientation the forward transform and its part of the exact inverse's orientation "
+            f"sum (the inverse's last per-volume step, 1/{len(V)} of its work, left out), one "
+            f"orientation per single-threaded numpy FP64 process, slowest {t:.1f} s")
+    return n * nvox / t, desc, n
+
+
 class OracleOnCores:
     """The FP64 oracle's forward transform and exact inverse of one volume,
     its orientations dealt over one single-threaded process per host core
@@ -781,6 +843,11 @@ def run_ours(args):
         cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc,
                "gpu_recon_rel_l2_vs_oracle": float(np.linalg.norm(fg - fo) / np.linalg.norm(fo)),
                "tubes32_no42": {"value": v1, "unit": UNIT, "cores": cores1, "sample": desc1}}
+        try:
+            v3, desc3, cores3 = oracle_sample_on_cores("splines256_no42")
+            cpu["splines256_no42"] = {"value": v3, "unit": UNIT, "cores": cores3, "sample": desc3}
+        except (OSError, MemoryError) as e:   # e.g. no room in the shared-memory file system
+            cpu["splines256_no42"] = {"unavailable": f"{type(e).__name__}: {e}"}
 
     if rank == 0:
         lat = sorted(step_ms)

@@ -59,3 +59,11 @@ def test_oracle_on_host_cores_equals_the_oracle():
         oc.close()
     assert dt > 0
     assert np.abs(out - ref).max() < 1e-12 * np.abs(ref).max()
+
+
+def test_oracle_sample_on_cores_runs_one_orientation_per_process():
+    """The bounded oracle sample of the large workload, here on the small one:
+    one orientation per process, the throughput over the slowest process."""
+    v, desc, n = bench.oracle_sample_on_cores("tubes32_no42", cores=3)
+    assert n == 3 and v > 0
+    assert desc.startswith("3 of the 42 orientations")
