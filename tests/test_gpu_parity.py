@@ -306,6 +306,35 @@ def test_degenerate_orientation_sets(M):
     _check_forward_inverse(M, dims, f, orient=np.stack([V[0], V[21]]), L=12)
 
 
+def test_degenerate_inputs(M):
+    """A constant volume (only w = 0, where every psi_hat_i = c_0): every U_i
+    is the constant c_0 f and the inverse returns f; the Nyquist checkerboard
+    (-1)^(x+y+z) (only the corner |w| = sqrt(3) pi, outside the ball): U = 0
+    and the inverse 0; the zero volume; a unit impulse against the oracle."""
+    import torch
+    dims = (32, 32, 32)
+    V = M.os3d_icosa_orientations(1)
+    bank = M.os3d_make_wavelets(dims, V, _params(M, L=12))
+    _, c = M.os3d_bank_coefficients(bank)
+    const = np.full(dims, 0.75, dtype=np.float32)
+    U = _to_np(M.os3d_forward(bank, _cuda(const)))[0]
+    assert np.abs(U - c[0] * 0.75).max() <= 2e-6 * abs(c[0] * 0.75)
+    fr = _to_np(M.os3d_inverse(bank, _cuda(U[None])))[0]
+    assert np.abs(fr - 0.75).max() <= 2e-6
+    z, y, x = np.meshgrid(*[np.arange(n) for n in dims], indexing="ij")
+    cb = ((-1.0) ** (z + y + x)).astype(np.float32)
+    U = _to_np(M.os3d_forward(bank, _cuda(cb)))[0]
+    assert np.abs(U).max() <= 1e-6
+    assert np.abs(_to_np(M.os3d_inverse(bank, _cuda(U[None])))[0]).max() <= 1e-6
+    zero = np.zeros(dims, dtype=np.float32)
+    U = _to_np(M.os3d_forward(bank, _cuda(zero)))[0]
+    assert not U.any()
+    imp = np.zeros(dims, dtype=np.float32)
+    imp[5, 17, 30] = 1.0
+    _check_forward_inverse(M, dims, imp, L=12)
+    torch.cuda.synchronize()
+
+
 def test_isotropic_wavelet_closed_form(M):
     """L = 0: h is the constant c_0, so every psi_hat_i = c_0 G and
     U_i = IDFT[c_0 G f_hat] for all i, with c_0 = 1/sqrt(N_o) (the
