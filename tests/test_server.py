@@ -11,7 +11,7 @@ pytestmark = pytest.mark.gpu
 
 TOL = 1e-5
 MIX = [((32, 32, 32), 1), ((48, 48, 48), 0), ((64, 64, 64), 1), ((32, 48, 64), 0),
-       ((32, 32, 32), 0), ((48, 48, 48), 1)]
+       ((32, 32, 32), 0), ((48, 48, 48), 1), ((16, 128, 160), 0)]
 
 
 def rel(a, b):
