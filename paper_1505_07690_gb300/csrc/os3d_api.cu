@@ -667,7 +667,8 @@ os3d_status os3d_make_wavelets(const int dims[3], const double* orient, int n_o,
   if (cudaMemcpyAsync(dslots.p, sl.data(), sizeof(double) * sl.size(), cudaMemcpyHostToDevice, s))
     return fail(OS3D_ECUDA);
   if (launch_bank_M(nz, ny, nx, p.N, p.gamma, p.eps, (const double*)dout.p + (L + 1), L,
-                    (const double*)dslots.p, nslots, n_o, b->Gs, b->GM, b->Minv, s) != cudaSuccess)
+                    (const double*)dslots.p, nslots, n_o, b->mirror, b->Gs, b->GM, b->Minv,
+                    s) != cudaSuccess)
     return fail(OS3D_ECUDA);
   // the temporaries are freed when this function returns: wait for the kernels
   if (cudaStreamSynchronize(s) != cudaSuccess) return fail(OS3D_ECUDA);

@@ -153,11 +153,15 @@ fit_kernel(const double* __restrict__ zt, const double* __restrict__ wt, int npt
 // A slot is an orientation a, optionally with its antipode b = -a; for the
 // pair h(t)^2 + h(-t)^2 = 2 (h_even^2 + h_odd^2).
 // Outputs (float): Gs = G / n^3, GM = G / (n^3 max(M, eps)), Minv = 1/max(M, eps)
-// (all zero outside the ball |w| < pi).
+// (all zero outside the ball |w| < pi). With `mirror` (every slot a pair, so
+// M(-w) = M(w)) only the planes iz <= nz/2 are computed and each value is
+// written at w and at -w; the recurrence gives h_even(-t) = h_even(t) and
+// h_odd(-t) = -h_odd(t) exactly, so a voxel reached from both sides gets the
+// same bits.
 __global__ void __launch_bounds__(256)
 bank_M_kernel(int nz, int ny, int nx, int N, double tscale, double eps,
               const double* __restrict__ cg, int L, const double* __restrict__ slots,
-              int nslots, int n_o, float* Gs, float* GM, float* Minv) {
+              int nslots, int n_o, int mirror, float* Gs, float* GM, float* Minv) {
   __shared__ double c[kMaxL + 1], al[kMaxL + 1], be[kMaxL + 1];
   __shared__ double sl[4 * 256];
   if (threadIdx.x <= L) {
@@ -167,16 +171,23 @@ bank_M_kernel(int nz, int ny, int nx, int N, double tscale, double eps,
     be[l] = double(l) / double(l + 1);
   }
   const long long nvox = (long long)nz * ny * nx;
+  const long long nwork = mirror ? (long long)(nz / 2 + 1) * ny * nx : nvox;
   const double inv_n = 1.0 / double(nvox);
   const long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long v0 = (long long)blockIdx.x * blockDim.x; v0 < nvox; v0 += stride) {
+  for (long long v0 = (long long)blockIdx.x * blockDim.x; v0 < nwork; v0 += stride) {
     const long long v = v0 + threadIdx.x;
     double M = 0.0, g = 0.0;
     bool inside = false;
     double wh[3] = {0.0, 0.0, 0.0};
     bool dc = false;
-    if (v < nvox) {
+    long long mv = -1;   // the voxel of -w, when it is written from here too
+    if (v < nwork) {
       const int ix = int(v % nx), iy = int((v / nx) % ny), iz = int(v / ((long long)nx * ny));
+      if (mirror) {
+        const long long m = ((long long)(iz ? nz - iz : 0) * ny + (iy ? ny - iy : 0)) * nx +
+                            (ix ? nx - ix : 0);
+        if (m != v) mv = m;
+      }
       const int kx = ix >= (nx + 1) / 2 ? ix - nx : ix;
       const int ky = iy >= (ny + 1) / 2 ? iy - ny : iy;
       const int kz = iz >= (nz + 1) / 2 ? iz - nz : iz;
@@ -223,18 +234,23 @@ bank_M_kernel(int nz, int ny, int nx, int N, double tscale, double eps,
         }
       }
     }
-    if (v < nvox) {
-      if (!inside) {
-        Gs[v] = 0.f;
-        GM[v] = 0.f;
-        Minv[v] = 0.f;
-      } else {
+    if (v < nwork) {
+      float gs = 0.f, gm = 0.f, mi = 0.f;
+      if (inside) {
         if (dc) M = double(n_o) * c[0] * c[0];
         M *= g * g;
         const double inv = 1.0 / fmax(M, eps);
-        Gs[v] = float(g * inv_n);
-        GM[v] = float(g * inv_n * inv);
-        Minv[v] = float(inv);
+        gs = float(g * inv_n);
+        gm = float(g * inv_n * inv);
+        mi = float(inv);
+      }
+      Gs[v] = gs;
+      GM[v] = gm;
+      Minv[v] = mi;
+      if (mv >= 0) {
+        Gs[mv] = gs;
+        GM[mv] = gm;
+        Minv[mv] = mi;
       }
     }
   }
@@ -251,13 +267,13 @@ cudaError_t launch_fit(const double* d_zt, const double* d_w, int npts, int mode
 
 cudaError_t launch_bank_M(int nz, int ny, int nx, int N, double gamma, double eps,
                           const double* d_c, int L, const double* d_slots, int nslots,
-                          int n_o, float* Gs, float* GM, float* Minv, cudaStream_t s) {
+                          int n_o, int mirror, float* Gs, float* GM, float* Minv, cudaStream_t s) {
   const double tscale = 2.0 * (gamma * kPiD) * (gamma * kPiD) / (1.0 + 2.0 * N);
   const long long nvox = (long long)nz * ny * nx;
   long long blocks = (nvox + 255) / 256;
   if (blocks > 152 * 16) blocks = 152 * 16;
   bank_M_kernel<<<(int)blocks, 256, 0, s>>>(nz, ny, nx, N, tscale, eps, d_c, L, d_slots, nslots,
-                                            n_o, Gs, GM, Minv);
+                                            n_o, mirror, Gs, GM, Minv);
   return cudaGetLastError();
 }
 

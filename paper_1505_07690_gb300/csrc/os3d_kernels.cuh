@@ -195,6 +195,7 @@ cudaError_t launch_fit(const double* d_z, const double* d_w, int npts, int mode,
                        cudaStream_t s);
 cudaError_t launch_bank_M(int nz, int ny, int nx, int N, double gamma, double eps,
                           const double* d_c, int L, const double* d_slots, int nslots,
-                          int n_o, float* Gs, float* GM, float* Minv, cudaStream_t s);
+                          int n_o, int mirror, float* Gs, float* GM, float* Minv,
+                          cudaStream_t s);
 
 }  // namespace os3d
