@@ -94,6 +94,24 @@ def test_minv_fp64(M):
     assert rel(mi, ob.M_inv()) < 1e-6
 
 
+@pytest.mark.parametrize("dims,paired", [((32, 48, 64), True), ((16, 16, 16), False),
+                                         ((16, 32, 48), True)])
+def test_minv_mirror_and_unpaired_sets(M, dims, paired):
+    """For an antipodally closed set the bank computes M on half of the grid
+    and writes it at w and -w: the table equals the oracle's and is symmetric
+    bit for bit; a set without antipodes takes every frequency itself."""
+    V = O.icosa_orientations(1)
+    if not paired:
+        V = V[:21].copy()
+    bank, ob = _pair(M, dims, orient=V, L=12)
+    mi = _to_np(M.os3d_bank_minv(bank))
+    assert rel(mi, ob.M_inv()) < 1e-6 and maxrel(mi, ob.M_inv()) < 2e-6
+    if paired:
+        mirror = mi[(-np.arange(dims[0])) % dims[0]][:, (-np.arange(dims[1])) % dims[1]][
+            :, :, (-np.arange(dims[2])) % dims[2]]
+        assert np.array_equal(mi.view(np.uint32), mirror.view(np.uint32))
+
+
 def _check_forward_inverse(M, dims, f, subdiv=1, orient=None, batch_oracle=True, **kw):
     bank, ob = _pair(M, dims, subdiv, orient, **kw)
     U = M.os3d_forward(bank, _cuda(f))
