@@ -1401,9 +1401,27 @@ os3d_status os3d_enhance_linear(const os3d_bank* b, const float* f, int batch, f
   e.half_dt = float(0.5 * dt);
   e.D11 = float(d->D11);
   e.D33 = float(d->D33);
-  for (int i = 0; i < b->n_o; ++i) {
-    for (int q = 0; q < 3; ++q) e.nvec[i][q] = float(b->orient[3 * i + q]);
-    for (int j = 0; j < b->n_o; ++j) e.Et[j * kEStride + i] = float(E[(size_t)i * b->n_o + j]);
+  // an antipodally closed set as its pairs (E = [[A, B], [B, A]]; the kernel
+  // takes C = A + B and D = A - B), else the full propagator
+  const int np2 = b->n_o / 2;
+  const int pb = b->mirror ? enhance_pair_block(b->n_o) : -1;
+  e.paired = pb > 0 && (int)b->slot_a.size() == np2;
+  if (e.paired) {
+    for (int i = 0; i < np2; ++i) {
+      const int ai = b->slot_a[i];
+      for (int q = 0; q < 3; ++q) e.nvec[i][q] = float(b->orient[3 * ai + q]);
+      for (int j = 0; j < np2; ++j) {
+        const double A = E[(size_t)ai * b->n_o + b->slot_a[j]];
+        const double B = E[(size_t)ai * b->n_o + b->slot_b[j]];
+        e.Et[j * kEStride + i] = float(A + B);
+        e.Et[(pb + j) * kEStride + pb + i] = float(A - B);
+      }
+    }
+  } else {
+    for (int i = 0; i < b->n_o; ++i) {
+      for (int q = 0; q < 3; ++q) e.nvec[i][q] = float(b->orient[3 * i + q]);
+      for (int j = 0; j < b->n_o; ++j) e.Et[j * kEStride + i] = float(E[(size_t)i * b->n_o + j]);
+    }
   }
   e.h = b->h;
   cudaStream_t s = (cudaStream_t)stream;

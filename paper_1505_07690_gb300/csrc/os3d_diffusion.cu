@@ -25,8 +25,39 @@ namespace {
 
 constexpr double kPiH = 3.141592653589793238462643383279502884;
 
+// Antipodally closed sets (PB > 0). L commutes with the antipodal
+// permutation, so with the pairs' first members first E = [[A, B], [B, A]],
+// and the spatial factors of n and -n are equal (r_i depends on (w.n_i)^2):
+// the Strang steps map s = v_a + v_b by C = A + B and d = v_a - v_b by
+// D = A - B independently. With h(t) = E(v) + t O(v) (even and odd parts):
+// s_0 = 2 E F, d_0 = 2 t O F, and h^T v = sum over pairs of E s + t O d.
+// Rows [0, PB) hold s, rows [PB, 2 PB) hold d (PB the pair count padded to a
+// multiple of R), so every warp's rows lie in one block and it reads only
+// that block's columns: half the multiply-adds of the full product.
+template <int EV>
+__device__ __forceinline__ void eval_h_parts(const HEval& h, float t, float& he, float& ho) {
+  if constexpr (EV < 2) {
+    constexpr int NE = EV == 0 ? 9 : 13;
+    constexpr int NO = NE - 1;
+    const float v = fmaf(t, t, -0.5f);
+    float e = h.e[NE - 1];
+#pragma unroll
+    for (int k = NE - 2; k >= 0; --k) e = fmaf(e, v, h.e[k]);
+    float o = h.o[NO - 1];
+#pragma unroll
+    for (int k = NO - 2; k >= 0; --k) o = fmaf(o, v, h.o[k]);
+    he = e;
+    ho = t * o;
+  } else {
+    const float hp = eval_h<EV>(h, t), hm = eval_h<EV>(h, -t);
+    he = 0.5f * (hp + hm);
+    ho = 0.5f * (hp - hm);
+  }
+}
+
 // One CTA per tile of TV = 128 listed frequencies, NP / R warps; NP = the
-// orientation count padded to a multiple of R rows per warp (R = 6 or 8).
+// orientation count padded to a multiple of R rows per warp (R = 6 or 8),
+// or for a closed set 2 PB rows.
 // Per Strang step warp w accumulates rows R w .. R w + R - 1 of E V, each
 // lane 4 consecutive frequencies: per propagator column j a lane reads its 4
 // vector entries with one 16-byte shared load and the R propagator entries,
@@ -41,11 +72,12 @@ constexpr size_t enhance_smem() {
          sizeof(int) * 2 * kTV;
 }
 
-template <int NP, int R, int EV>
+template <int NP, int R, int EV, int PB = 0>
 __global__ void __launch_bounds__(32 * NP / R)
 enhance_kernel(const __grid_constant__ EnhanceArgs a) {
   static_assert(R % 2 == 0 && NP % R == 0 && NP % 2 == 0 && NP <= kEStride,
                 "R propagator rows per warp, in pairs; NP^2 floats keep V 16-byte aligned");
+  static_assert(PB == 0 || (2 * PB == NP && PB % R == 0), "each warp's rows in one block");
   constexpr int NT = 32 * NP / R, TV = kTV;
   extern __shared__ __align__(16) float esm[];
   float* Es = esm;                       // Es[j * NP + i] = E[i][j]
@@ -57,10 +89,26 @@ enhance_kernel(const __grid_constant__ EnhanceArgs a) {
   int* mvox = vox + TV;
   const int t = threadIdx.x;
   const int i0 = R * (t >> 5), q0 = 4 * (t & 31);
-  const int nj = (a.n_o + 1) & ~1;       // columns j >= n_o of E are zero; nj <= NP
+  // columns of E this warp reads: [jb, jb + nj) (zero beyond n_o, or beyond
+  // the pair count in each block)
+  const int np2 = a.n_o / 2;
+  const int nj = PB ? (np2 + 1) & ~1 : (a.n_o + 1) & ~1;
+  const int jb = (PB && i0 >= PB) ? PB : 0;
+  // row i's orientation (paired: its pair's first member), or -1 for padding
+  auto orient_of = [&](int i) {
+    if constexpr (PB > 0) {
+      const int r = i < PB ? i : i - PB;
+      return r < np2 ? r : -1;
+    } else {
+      return i < a.n_o ? i : -1;
+    }
+  };
 
   for (int q = t; q < NP * NP; q += NT) Es[q] = a.Et[(q / NP) * kEStride + q % NP];
-  for (int q = t; q < 3 * NP; q += NT) nv[q] = (q / 3 < a.n_o) ? a.nvec[q / 3][q % 3] : 0.f;
+  for (int q = t; q < 3 * NP; q += NT) {
+    const int o = PB ? (q / 3 < np2 ? q / 3 : -1) : (q / 3 < a.n_o ? q / 3 : -1);
+    nv[q] = o >= 0 ? a.nvec[o][q % 3] : 0.f;
+  }
 
   const int ntiles = (a.n_in + TV - 1) / TV;
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
@@ -101,12 +149,19 @@ enhance_kernel(const __grid_constant__ EnhanceArgs a) {
     // ---- F and the initial vector h F
     for (int p = t; p < NP * TV; p += NT) {
       const int i = p / TV, q = p % TV;
+      const int o = orient_of(i);
       float f = 1.f, hv = 0.f;
-      if (vox[q] >= 0) {
-        const float tau = fmaf(geo[q], nv[3 * i], fmaf(geo[TV + q], nv[3 * i + 1], geo[2 * TV + q] * nv[3 * i + 2]));
+      if (vox[q] >= 0 && o >= 0) {
+        const float tau = fmaf(geo[q], nv[3 * o], fmaf(geo[TV + q], nv[3 * o + 1], geo[2 * TV + q] * nv[3 * o + 2]));
         const float r2 = geo[4 * TV + q];
         f = expf(-a.half_dt * fmaf(a.D11, r2 - tau * tau, a.D33 * tau * tau));
-        if (i < a.n_o) hv = r2 > 0.f ? eval_h<EV>(a.h, tau * geo[3 * TV + q]) : a.h.c0;
+        if constexpr (PB > 0) {   // s_0 = 2 E F, d_0 = 2 t O F
+          float he = a.h.c0, ho = 0.f;
+          if (r2 > 0.f) eval_h_parts<EV>(a.h, tau * geo[3 * TV + q], he, ho);
+          hv = 2.f * (i < PB ? he : ho);
+        } else {
+          hv = r2 > 0.f ? eval_h<EV>(a.h, tau * geo[3 * TV + q]) : a.h.c0;
+        }
       }
       F[i * TV + q] = f;
       V[i * TV + q] = hv * f;
@@ -120,7 +175,7 @@ enhance_kernel(const __grid_constant__ EnhanceArgs a) {
 #pragma unroll
         for (int c = 0; c < 4; ++c) acc[r][c] = make_float2(0.f, 0.f);
 #pragma unroll 1
-      for (int j0 = 0; j0 < nj; j0 += 2) {
+      for (int j0 = jb; j0 < jb + nj; j0 += 2) {
 #pragma unroll
         for (int jj = 0; jj < 2; ++jj) {
           const int j = j0 + jj;
@@ -161,10 +216,17 @@ enhance_kernel(const __grid_constant__ EnhanceArgs a) {
     // ---- m = n^3 h^T V per slot (products in place, then column sums)
     for (int p = t; p < NP * TV; p += NT) {
       const int i = p / TV, q = p % TV;
+      const int o = orient_of(i);
       float hv = 0.f;
-      if (vox[q] >= 0 && i < a.n_o) {
-        const float tau = fmaf(geo[q], nv[3 * i], fmaf(geo[TV + q], nv[3 * i + 1], geo[2 * TV + q] * nv[3 * i + 2]));
-        hv = geo[4 * TV + q] > 0.f ? eval_h<EV>(a.h, tau * geo[3 * TV + q]) : a.h.c0;
+      if (vox[q] >= 0 && o >= 0) {
+        const float tau = fmaf(geo[q], nv[3 * o], fmaf(geo[TV + q], nv[3 * o + 1], geo[2 * TV + q] * nv[3 * o + 2]));
+        if constexpr (PB > 0) {   // h^T v = sum E s + t O d
+          float he = a.h.c0, ho = 0.f;
+          if (geo[4 * TV + q] > 0.f) eval_h_parts<EV>(a.h, tau * geo[3 * TV + q], he, ho);
+          hv = i < PB ? he : ho;
+        } else {
+          hv = geo[4 * TV + q] > 0.f ? eval_h<EV>(a.h, tau * geo[3 * TV + q]) : a.h.c0;
+        }
       }
       V[i * TV + q] *= hv;
     }
@@ -172,7 +234,7 @@ enhance_kernel(const __grid_constant__ EnhanceArgs a) {
     for (int q = t; q < TV; q += NT) {
       if (vox[q] < 0) continue;
       float sum = 0.f;
-      for (int i = 0; i < a.n_o; ++i) sum += V[i * TV + q];
+      for (int i = 0; i < (PB ? NP : a.n_o); ++i) sum += V[i * TV + q];
       const float m = sum * a.n3;
       const float2 fh = a.fh[vox[q]];
       a.A[vox[q]] = make_float2(fh.x * m, fh.y * m);
@@ -184,15 +246,15 @@ enhance_kernel(const __grid_constant__ EnhanceArgs a) {
   }
 }
 
-template <int NP, int R>
+template <int NP, int R, int PB = 0>
 cudaError_t launch_np(const EnhanceArgs& a, int ev, cudaStream_t s) {
   constexpr int NT = 32 * NP / R;
   int dev = 0, nsm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   constexpr size_t sm = enhance_smem<NP>();
-  auto k = ev == 0 ? enhance_kernel<NP, R, 0>
-                    : (ev == 1 ? enhance_kernel<NP, R, 1> : enhance_kernel<NP, R, 2>);
+  auto k = ev == 0 ? enhance_kernel<NP, R, 0, PB>
+                    : (ev == 1 ? enhance_kernel<NP, R, 1, PB> : enhance_kernel<NP, R, 2, PB>);
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   int per_sm = 1;
@@ -357,8 +419,24 @@ int angular_propagator(const double* V, int n, int sh_degree, double tau, std::v
   return l;
 }
 
+int enhance_pair_block(int n_o) {
+  for (int pb : {4, 6, 12, 24, 36})
+    if (n_o / 2 <= pb) return pb;
+  return -1;
+}
+
 cudaError_t launch_enhance(const EnhanceArgs& a, int ev, cudaStream_t s) {
   const int n = a.n_o;
+  if (a.paired) {   // (2 PB rows, rows per warp, PB)
+    switch (enhance_pair_block(n)) {
+      case 4: return launch_np<8, 4, 4>(a, ev, s);
+      case 6: return launch_np<12, 6, 6>(a, ev, s);
+      case 12: return launch_np<24, 6, 12>(a, ev, s);
+      case 24: return launch_np<48, 8, 24>(a, ev, s);
+      case 36: return launch_np<72, 6, 36>(a, ev, s);
+      default: return cudaErrorInvalidValue;
+    }
+  }
   // (rows, rows per warp): no padding for the 12- and 42-orientation sets
   if (n <= 8) return launch_np<8, 8>(a, ev, s);
   if (n <= 12) return launch_np<12, 6>(a, ev, s);

@@ -145,12 +145,17 @@ struct EnhanceArgs {
   int steps;                  // Strang steps K
   float half_dt;              // t / (2K)
   float D11, D33;
-  float nvec[kMaxOrientE][3];
+  int paired;                 // 1: an antipodally closed set, integrated as its n_o/2 pairs
+  float nvec[kMaxOrientE][3];      // orientations (paired: the pairs' first members)
   float Et[kEStride * kEStride];   // exp(dt D44 L) transposed: Et[j kEStride + i] = E[i][j],
-                                   // zero outside i, j < n_o
+                                   // zero outside i, j < n_o; paired: the blocks C = A + B
+                                   // (rows and columns 0 ..) and D = A - B (from the
+                                   // kernel's block offset) of E = [[A, B], [B, A]]
   HEval h;
 };
 cudaError_t launch_enhance(const EnhanceArgs& a, int ev, cudaStream_t s);
+// rows per block of the paired integration for a closed set of n_o vectors, or -1
+int enhance_pair_block(int n_o);
 // The same integration with the propagator product on the tensor cores
 // (os3d_diffusion_tc.cu), for orientation sets of up to 176 vectors.
 struct EnhanceTCArgs {
