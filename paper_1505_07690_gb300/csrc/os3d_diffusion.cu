@@ -432,7 +432,7 @@ cudaError_t launch_enhance(const EnhanceArgs& a, int ev, cudaStream_t s) {
       case 4: return launch_np<8, 4, 4>(a, ev, s);
       case 6: return launch_np<12, 6, 6>(a, ev, s);
       case 12: return launch_np<24, 6, 12>(a, ev, s);
-      case 24: return launch_np<48, 8, 24>(a, ev, s);
+      case 24: return launch_np<48, 6, 24>(a, ev, s);
       case 36: return launch_np<72, 6, 36>(a, ev, s);
       default: return cudaErrorInvalidValue;
     }
