@@ -2,7 +2,8 @@
 //
 // The 3D DFT of every orientation is split into a z-pass (DFT along z of
 // 16-wide pencil tiles) and an xy-pass (2D DFT of z-planes: a whole plane per
-// CTA, or an 8-CTA cluster per 256^2 plane), with the per-orientation
+// CTA, or for 256^2 planes an 8-CTA cluster per plane, and in the forward
+// transform four independent quarter-plane CTAs), with the per-orientation
 // intermediate T passed through L2:
 //   forward  (Eq. construction1Discrete):  U_a = IDFT_xy IDFT_z [ f_hat G h_a ]
 //            z-pass : f_hat tile (read once per block) x h(w_hat . n_a) -> IDFT_z -> T_a
@@ -608,6 +609,204 @@ xy_kernel(const __grid_constant__ PassArgs a) {
 }
 
 // ----------------------------------------------------------------------------
+// Forward score pass (T_s -> IDFT_xy -> U_a, U_b = conj U_a) for planes too
+// large for one CTA (256^2), as F = 4 independent quarter-plane transforms
+// split by the output row modulo F.
+// The rows y = F k + h (h < F) of the 2D DFT of an NY x NX plane a are the
+// (NY/F)-point DFT along y of the folded rows
+//   b_h[r] = W^{h r} sum_{q < F} a[r + (NY/F) q] w_F^{h q},   r < NY/F,
+// W = exp(DIR 2 pi i / NY), w_F = W^{NY/F} (split the input row as
+// r + (NY/F) q: W^{(r + (NY/F) q)(F k + h)} = W_{NY/F}^{r k} W^{h r} w_F^{h q}).
+// So each quarter is a whole (NY/F) x NX plane transform in one CTA (the
+// machinery of xy_kernel on a 64 x 256 plane, 512 threads, 137 KB), with no
+// exchange between CTAs: the CTA reads the whole input plane (the four
+// quarters of a plane run on consecutive CTAs, so three of the four reads of
+// each input row come from L2) and writes every F-th output row. At
+// 256^3 x 42 this forward pass takes 3.3-3.4 instead of 4.2 ms per step
+// (complex64; BF16 scores 2.5 instead of 3.6 ms) against the 8-CTA cluster
+// pass; the inverse stays on the cluster pass, where the four reads of both
+// U_a and U_b per part made the same fold slower (6.2 against 3.9 ms).
+// ----------------------------------------------------------------------------
+template <int NY, int NX> struct XYFold { static constexpr int F = 1; };
+template <> struct XYFold<256, 256> { static constexpr int F = 4; };
+
+template <int NY, int NX>
+struct XYFoldCfg {
+  static constexpr int F = XYFold<NY, NX>::F;
+  static constexpr int NH = NY / F;
+  using C = XYCfg<NH, NX, 1, 512>;
+  // work buffer, twiddles along x (NX) and y (NH), fold factors W^m (m < NY)
+  static constexpr size_t smem_bytes = sizeof(float2) * (size_t(C::BUF) + NX + NH + NY);
+};
+
+template <int NY, int NX, int UBF16>
+__global__ void __launch_bounds__(XYFoldCfg<NY, NX>::C::NT, 1)
+xy_fold_kernel(const __grid_constant__ PassArgs a) {
+  using FC = XYFoldCfg<NY, NX>;
+  using C = typename FC::C;
+  constexpr int F = FC::F, NH = FC::NH;
+  constexpr int R1x = C::R1x, R2x = C::R2x, R1y = C::R1y, R2y = C::R2y;
+  constexpr int NT = C::NT;
+  constexpr int DIR = +1;
+  static_assert(F == 4, "quarter planes");
+  static_assert(NY % F == 0 && C::NYH == NH && C::NXH == NX, "one part of a plane per CTA");
+
+  extern __shared__ __align__(16) float2 sm[];
+  float2* work = sm;
+  float2* twx = sm + C::BUF;
+  float2* twy = twx + NX;
+  float2* twf = twy + NH;   // W^m, m < NY: the fold factors
+
+  const int t = threadIdx.x;
+  const long long P = (long long)NY * NX;
+  const long long PART = (long long)NH * NX;   // elements of one part of a plane
+  const int nunits = F * a.nz * a.nslots;
+
+  fill_twiddles<NX, DIR>(twx);
+  fill_twiddles<NH, DIR>(twy);
+  fill_twiddles<NY, DIR>(twf);
+  __syncthreads();
+
+  // T_s at element e of the plane (row y, column x); zero on the tiles
+  // outside the disc, which the z-pass does not write
+  auto input = [&](int s, long long e, int y, int x) -> float2 {
+    return (a.disc && tile_outside(x, y, NX, NY))
+               ? make_float2(0.f, 0.f)
+               : reinterpret_cast<const float2*>(a.in)[(long long)s * a.slot_stride + e];
+  };
+
+  for (int u = blockIdx.x; u < nunits; u += gridDim.x) {
+    const int hf = u % F, pl = u / F;
+    const int z = pl % a.nz, s = pl / a.nz;
+    const long long zoff = (long long)z * P;
+    // ---- x direction, step 1 on the folded rows (global -> registers -> shared)
+    {
+      const int n2 = t % R2x, r0 = t / R2x;
+      float2 tw[R1x];
+#pragma unroll
+      for (int k1 = 0; k1 < R1x; ++k1) tw[k1] = twx[(n2 * k1) % NX];
+#pragma unroll
+      for (int j = 0; j < C::JX1; ++j) {
+        const int r = r0 + (NT / R2x) * j;
+        const long long row = zoff + (long long)r * NX;
+        float2 v[R1x];
+#pragma unroll
+        for (int n1 = 0; n1 < R1x; ++n1) v[n1] = input(s, row + n2 + R2x * n1, r, n2 + R2x * n1);
+#pragma unroll
+        for (int q = 1; q < F; ++q) {
+          float2 w[R1x];
+#pragma unroll
+          for (int n1 = 0; n1 < R1x; ++n1)
+            w[n1] = input(s, row + q * PART + n2 + R2x * n1, r + q * NH, n2 + R2x * n1);
+          // x w_F^{h q}, the same power for the whole CTA
+          switch ((q * hf) & (F - 1)) {
+            case 0:
+#pragma unroll
+              for (int n1 = 0; n1 < R1x; ++n1) v[n1] = cadd(v[n1], w[n1]);
+              break;
+            case 1:
+#pragma unroll
+              for (int n1 = 0; n1 < R1x; ++n1) v[n1] = cadd(v[n1], cmul_i<DIR>(w[n1]));
+              break;
+            case 2:
+#pragma unroll
+              for (int n1 = 0; n1 < R1x; ++n1) v[n1] = csub(v[n1], w[n1]);
+              break;
+            default:
+#pragma unroll
+              for (int n1 = 0; n1 < R1x; ++n1) v[n1] = cadd(v[n1], cmul_i<-DIR>(w[n1]));
+              break;
+          }
+        }
+        if (hf) {
+          const float2 om = twf[r * hf];
+#pragma unroll
+          for (int n1 = 0; n1 < R1x; ++n1) v[n1] = cmul(v[n1], om);
+        }
+        dft<R1x, DIR>(v);
+#pragma unroll
+        for (int k1 = 0; k1 < R1x; ++k1)
+          work[C::xphys(r, n2 + R2x * k1)] = (k1 == 0) ? v[k1] : cmul(v[k1], tw[k1]);
+      }
+    }
+    __syncthreads();
+    // this CTA's part of the rows of its next unit's input plane goes to L2
+    // while this unit runs (the F CTAs of a plane cover it together)
+    if (t == 0 && u + (int)gridDim.x < nunits) {
+      const int un = u + (int)gridDim.x;
+      const int pn = un / F, hn = un % F;
+      const int zn = pn % a.nz, sn = pn / a.nz;
+      const long long base = (long long)zn * P + hn * PART;
+      prefetch_l2(reinterpret_cast<const float2*>(a.in) + (long long)sn * a.slot_stride + base,
+                  (unsigned)(NH * NX * sizeof(float2)));
+    }
+    // ---- x direction, step 2 (x layout -> y layout, in the same buffer)
+    {
+      float2 w[C::JX3][R2x];
+#pragma unroll
+      for (int j = 0; j < C::JX3; ++j) {
+        int r, k1;
+        C::x2_item(t, j, r, k1);
+#pragma unroll
+        for (int m = 0; m < R2x; ++m) w[j][m] = work[C::xphys(r, m + R2x * k1)];
+        dft<R2x, DIR>(w[j]);
+      }
+      __syncthreads();   // every x-layout read is done before the y layout is written
+#pragma unroll
+      for (int j = 0; j < C::JX3; ++j) {
+        int r, k1;
+        C::x2_item(t, j, r, k1);
+#pragma unroll
+        for (int k2 = 0; k2 < R2x; ++k2) work[r * C::PY + k1 + R1x * k2] = w[j][k2];
+      }
+      __syncthreads();
+    }
+    // ---- y direction (NY/F points), step 1 (in place)
+    {
+      const int n2 = t / C::CW;
+      float2 tw[R1y];
+#pragma unroll
+      for (int k1 = 0; k1 < R1y; ++k1) tw[k1] = twy[(n2 * k1) % NH];
+#pragma unroll
+      for (int j = 0; j < C::JY1; ++j) {
+        const int c = t % C::CW + C::CW * j;
+        if (NX % C::CW != 0 && c >= NX) break;
+        float2 u1[R1y];
+#pragma unroll
+        for (int n1 = 0; n1 < R1y; ++n1) u1[n1] = work[(n2 + R2y * n1) * C::PY + c];
+        dft<R1y, DIR>(u1);
+#pragma unroll
+        for (int k1 = 0; k1 < R1y; ++k1)
+          work[(n2 + R2y * k1) * C::PY + c] = (k1 == 0) ? u1[k1] : cmul(u1[k1], tw[k1]);
+      }
+    }
+    __syncthreads();
+    // ---- y direction, step 2 + store of the output rows F k + h
+    {
+      const long long o = a.ua[s], ob = a.ub[s];
+#pragma unroll
+      for (int j = 0; j < C::JY3; ++j) {
+        const int q = t + NT * j;
+        const int c = q % NX, k1 = q / NX;
+        float2 w[R2y];
+#pragma unroll
+        for (int m = 0; m < R2y; ++m) w[m] = work[(m + R2y * k1) * C::PY + c];
+        dft<R2y, DIR>(w);
+#pragma unroll
+        for (int k2 = 0; k2 < R2y; ++k2) {
+          const int y = F * (k1 + R1y * k2) + hf;
+          const long long e = zoff + (long long)y * NX + c;
+          store_u<UBF16>(a.out, o + e, w[k2]);
+          if (ob >= 0) store_u<UBF16>(a.out, ob + e, cconj(w[k2]));
+        }
+      }
+    }
+    __syncthreads();   // work is rewritten by the next unit
+  }
+}
+
+
+// ----------------------------------------------------------------------------
 // Score-domain step of Upsilon = W^{*,ext} Phi W (Sec. 4.1) for one block of
 // orientation pairs, fused into one plane pass, in place on T_s:
 //   T_s <- DFT_xy[ m_s Phi( IDFT_xy T_s ) ]
@@ -953,8 +1152,34 @@ cudaError_t launch_xy_one(const PassArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// the forward score pass on folded parts of planes (xy_fold_kernel): as many
+// CTAs as are resident at once, a multiple of F so that the parts of a plane
+// run side by side
+template <int NY, int NX, int UB>
+cudaError_t launch_xy_fold_one(const PassArgs& a, cudaStream_t s) {
+  using FC = XYFoldCfg<NY, NX>;
+  constexpr int F = FC::F;
+  auto k = xy_fold_kernel<NY, NX, UB>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)FC::smem_bytes);
+  if (e != cudaSuccess) return e;
+  int dev = 0, nsm = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, FC::C::NT, FC::smem_bytes);
+  if (e != cudaSuccess) return e;
+  const int units = F * a.nz * a.nslots;
+  const int grid = std::max(F, std::min(units, std::max(1, per_sm) * nsm) / F * F);
+  k<<<grid, FC::C::NT, FC::smem_bytes, s>>>(a);
+  return cudaGetLastError();
+}
+
 template <int NY, int NX>
 cudaError_t launch_xy_n(int mode, int ub, const PassArgs& a, cudaStream_t s) {
+  if constexpr (XYFold<NY, NX>::F > 1) {
+    if (mode == XY_FWD_SCORE)
+      return ub ? launch_xy_fold_one<NY, NX, 1>(a, s) : launch_xy_fold_one<NY, NX, 0>(a, s);
+  }
   switch (mode) {
     case XY_FWD_REAL: return launch_xy_one<NY, NX, XY_FWD_REAL, 0>(a, s);
     case XY_INV_REAL: return launch_xy_one<NY, NX, XY_INV_REAL, 0>(a, s);
