@@ -395,8 +395,9 @@ def test_batch_zero_is_rejected(M):
 
 
 def test_plane_pass_256_squared(M):
-    """256^2 planes take the plane pass on 8-CTA clusters (an eighth of a plane
-    per CTA); 32 x 256 x 256 keeps the oracle fast."""
+    """256^2 planes: the forward score pass on four quarter-plane CTAs per
+    plane (output rows folded modulo 4), the inverse on 8-CTA clusters (an
+    eighth of a plane per CTA); 32 x 256 x 256 keeps the oracle fast."""
     dims = (32, 256, 256)
     f = synth.straight_tubes(dims, 3, seed=54, noise=0.1)
     _check_forward_inverse(M, dims, f, subdiv=0, L=12, block_slots=4)
@@ -404,6 +405,29 @@ def test_plane_pass_256_squared(M):
     bank, ob = _pair(M, dims, subdiv=0, L=12, block_slots=4)
     fu = _to_np(M.os3d_upsilon(bank, _cuda(f), 1.5))
     assert rel(fu, O.upsilon(f, ob, 1.5)) <= TOL
+
+
+def test_quarter_plane_forward_unpaired_batch_and_bf16(M):
+    """The quarter-plane forward pass of 256^2 planes with orientations that
+    have no antipode (U_a only), a batch of two volumes and ragged blocks of 4
+    slots, against the oracle; and with BF16 scores, against the oracle and
+    against the complex64 scores of the same call."""
+    import torch
+    dims = (16, 256, 256)
+    fs = [synth.straight_tubes(dims, 3, seed=s, noise=0.1) for s in (71, 72)]
+    V = O.icosa_orientations(1)[:21].copy()
+    bank, ob = _pair(M, dims, orient=V, L=12, block_slots=4)
+    U = _to_np(M.os3d_forward(bank, torch.from_numpy(np.stack(fs)).cuda()))
+    for v in range(2):
+        assert close(U[v], O.forward(fs[v], ob)), v
+    bank2, ob2 = _pair(M, dims, subdiv=0, L=12)
+    fd = _cuda(fs[0])
+    Uc = _to_np(M.os3d_forward(bank2, fd))[0]
+    Ub = M.os3d_forward(bank2, fd, bf16=True).float().cpu().numpy()[0]
+    Ub = Ub[..., 0] + 1j * Ub[..., 1]
+    assert close(Uc, O.forward(fs[0], ob2))
+    assert close(Ub, O.forward(fs[0], ob2), bf16=True)
+    assert rel(Ub, Uc) <= 4e-3
 
 
 def test_default_workspace_is_allocated_on_first_use(M):
