@@ -30,7 +30,8 @@ struct HEval {
 //  Z_INV_FINAL: A x mult (G/(n^3 max(M,eps))) -> IDFT_z           -> T0
 enum ZMode { Z_FWD_PREP = 0, Z_FWD_SCORE = 1, Z_INV_SCORE = 2, Z_INV_FINAL = 3 };
 // xy-passes (2D DFT of z-planes: a whole plane per CTA; 256^2 planes: an 8-CTA cluster
-// per plane, XY_FWD_SCORE four independent quarter-plane CTAs):
+// per plane; XY_FWD_SCORE on 256^2 planes four independent quarter-plane CTAs, on
+// 128^2 planes with complex64 scores two half-plane CTAs):
 //  XY_FWD_REAL : f (real) -> DFT_xy                                -> T0
 //  XY_FWD_SCORE: T_s -> IDFT_xy -> U_a, U_b = conj U_a              (HBM store)
 //  XY_INV_SCORE: U_a + conj U_b (HBM load) -> DFT_xy               -> T_s

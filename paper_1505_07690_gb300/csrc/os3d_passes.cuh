@@ -2,8 +2,9 @@
 //
 // The 3D DFT of every orientation is split into a z-pass (DFT along z of
 // 16-wide pencil tiles) and an xy-pass (2D DFT of z-planes: a whole plane per
-// CTA, or for 256^2 planes an 8-CTA cluster per plane, and in the forward
-// transform four independent quarter-plane CTAs), with the per-orientation
+// CTA, or for 256^2 planes an 8-CTA cluster per plane; the forward score pass
+// on 256^2 planes as four independent quarter-plane CTAs and on 128^2 planes
+// with complex64 scores as two half-plane CTAs), with the per-orientation
 // intermediate T passed through L2:
 //   forward  (Eq. construction1Discrete):  U_a = IDFT_xy IDFT_z [ f_hat G h_a ]
 //            z-pass : f_hat tile (read once per block) x h(w_hat . n_a) -> IDFT_z -> T_a
@@ -609,38 +610,45 @@ xy_kernel(const __grid_constant__ PassArgs a) {
 }
 
 // ----------------------------------------------------------------------------
-// Forward score pass (T_s -> IDFT_xy -> U_a, U_b = conj U_a) for planes too
-// large for one CTA (256^2), as F = 4 independent quarter-plane transforms
-// split by the output row modulo F.
+// Forward score pass (T_s -> IDFT_xy -> U_a, U_b = conj U_a) on F independent
+// parts of each plane split by the output row modulo F: F = 4 for 256^2
+// planes, too large for one CTA, and F = 2 for 128^2 planes (two half-plane
+// CTAs of 256 threads and 72 KB per SM; a CTA that runs alone on its SM
+// leaves room for z-pass CTAs of the other stream beside it).
 // The rows y = F k + h (h < F) of the 2D DFT of an NY x NX plane a are the
 // (NY/F)-point DFT along y of the folded rows
 //   b_h[r] = W^{h r} sum_{q < F} a[r + (NY/F) q] w_F^{h q},   r < NY/F,
 // W = exp(DIR 2 pi i / NY), w_F = W^{NY/F} (split the input row as
 // r + (NY/F) q: W^{(r + (NY/F) q)(F k + h)} = W_{NY/F}^{r k} W^{h r} w_F^{h q}).
-// So each quarter is a whole (NY/F) x NX plane transform in one CTA (the
-// machinery of xy_kernel on a 64 x 256 plane, 512 threads, 137 KB), with no
-// exchange between CTAs: the CTA reads the whole input plane (the four
-// quarters of a plane run on consecutive CTAs, so three of the four reads of
-// each input row come from L2) and writes every F-th output row. At
+// So each part is a whole (NY/F) x NX plane transform in one CTA (the
+// machinery of xy_kernel on a 64 x 256 or 64 x 128 plane), with no exchange
+// between CTAs: the CTA reads the whole input plane (the F parts of a plane
+// run on consecutive CTAs, so all but one of the F reads of each input row
+// come from L2) and writes every F-th output row. At
 // 256^3 x 42 this forward pass takes 3.3-3.4 instead of 4.2 ms per step
 // (complex64; BF16 scores 2.5 instead of 3.6 ms) against the 8-CTA cluster
 // pass; the inverse stays on the cluster pass, where the four reads of both
-// U_a and U_b per part made the same fold slower (6.2 against 3.9 ms).
+// U_a and U_b per part made the same fold slower (6.2 against 3.9 ms). At
+// 128^3 x 162 the halves take the forward + inverse step from 2.087 to
+// 2.063 ms (complex64): the half-plane pass itself is no faster, but the
+// z-pass beside it is (0.69 against 0.78 ms per step).
 // ----------------------------------------------------------------------------
 template <int NY, int NX> struct XYFold { static constexpr int F = 1; };
 template <> struct XYFold<256, 256> { static constexpr int F = 4; };
+template <> struct XYFold<128, 128> { static constexpr int F = 2; };
 
 template <int NY, int NX>
 struct XYFoldCfg {
   static constexpr int F = XYFold<NY, NX>::F;
   static constexpr int NH = NY / F;
-  using C = XYCfg<NH, NX, 1, 512>;
+  static constexpr int MINB = F == 2 ? 2 : 1;   // CTAs per SM
+  using C = XYCfg<NH, NX, 1, 512 / MINB>;
   // work buffer, twiddles along x (NX) and y (NH), fold factors W^m (m < NY)
   static constexpr size_t smem_bytes = sizeof(float2) * (size_t(C::BUF) + NX + NH + NY);
 };
 
 template <int NY, int NX, int UBF16>
-__global__ void __launch_bounds__(XYFoldCfg<NY, NX>::C::NT, 1)
+__global__ void __launch_bounds__(XYFoldCfg<NY, NX>::C::NT, XYFoldCfg<NY, NX>::MINB)
 xy_fold_kernel(const __grid_constant__ PassArgs a) {
   using FC = XYFoldCfg<NY, NX>;
   using C = typename FC::C;
@@ -648,7 +656,7 @@ xy_fold_kernel(const __grid_constant__ PassArgs a) {
   constexpr int R1x = C::R1x, R2x = C::R2x, R1y = C::R1y, R2y = C::R2y;
   constexpr int NT = C::NT;
   constexpr int DIR = +1;
-  static_assert(F == 4, "quarter planes");
+  static_assert(F == 2 || F == 4, "halves or quarters of planes");
   static_assert(NY % F == 0 && C::NYH == NH && C::NXH == NX, "one part of a plane per CTA");
 
   extern __shared__ __align__(16) float2 sm[];
@@ -699,7 +707,7 @@ xy_fold_kernel(const __grid_constant__ PassArgs a) {
           for (int n1 = 0; n1 < R1x; ++n1)
             w[n1] = input(s, row + q * PART + n2 + R2x * n1, r + q * NH, n2 + R2x * n1);
           // x w_F^{h q}, the same power for the whole CTA
-          switch ((q * hf) & (F - 1)) {
+          switch ((q * hf * (4 / F)) & 3) {
             case 0:
 #pragma unroll
               for (int n1 = 0; n1 < R1x; ++n1) v[n1] = cadd(v[n1], w[n1]);
@@ -1176,9 +1184,13 @@ cudaError_t launch_xy_fold_one(const PassArgs& a, cudaStream_t s) {
 
 template <int NY, int NX>
 cudaError_t launch_xy_n(int mode, int ub, const PassArgs& a, cudaStream_t s) {
-  if constexpr (XYFold<NY, NX>::F > 1) {
+  if constexpr (XYFold<NY, NX>::F == 4) {
     if (mode == XY_FWD_SCORE)
       return ub ? launch_xy_fold_one<NY, NX, 1>(a, s) : launch_xy_fold_one<NY, NX, 0>(a, s);
+  } else if constexpr (XYFold<NY, NX>::F == 2) {
+    // halves of 128^2 planes for complex64 scores only (with BF16 scores the
+    // whole-plane pass measured 0.5 % faster per step)
+    if (mode == XY_FWD_SCORE && !ub) return launch_xy_fold_one<NY, NX, 0>(a, s);
   }
   switch (mode) {
     case XY_FWD_REAL: return launch_xy_one<NY, NX, XY_FWD_REAL, 0>(a, s);
